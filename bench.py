@@ -1,0 +1,372 @@
+"""Benchmark: fringe-fit trials/s of the cross-spectrum single-pulse search.
+
+One step = the whole hot path (dedispersion shift table, FP64 channel
+normalisation, calibration, dedispersion, delay FFT, window/rate FFTs, peak
+search, FP64 series statistics + threshold, window match, host
+cross-baseline match) over one EVN-scale scan segment: 15 baselines x
+58,594 APs x 512 frequency points (3.6 GB complex64, larger than L2),
+501 DM trials 0..1000, windows 1..32 AP, delay pad 4, rate pad 4, FP32.
+A trial is one (baseline, DM trial, window, segment) fringe fit.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun each rank searches its own scan (weak scaling, no collective
+on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fringe-fit trials/sec (baseline x DM x window x segment), EVN-scale scan"
+UNIT = "trials/s"
+SM_COUNT, FP32_LANES = 148, 128
+
+
+def workload():
+    from paper_2108_05602_b300 import synth
+    return synth.evn()
+
+
+def trial_count(wl, nvalid) -> int:
+    n = 0
+    for nv in nvalid:
+        nv = max(int(nv), 0)
+        n += sum(nv // w for w in wl.windows)
+    return n * wl.n_bl
+
+
+def algorithmic_flops(wl, nvalid) -> float:
+    """Nominal flops of one search: 5 N log2 N per complex N-point FFT
+    (delay transform of each dedispersed AP over M = 4 N_f points; rate
+    transform of each segment's delay column over R = 4 w points), 3 per
+    |Z|^2 cell, 2 (w - 1) per coherent sum when R = 1."""
+    M = wl.pad_delay * wl.n_f
+    tot = 0.0
+    for nv in nvalid:
+        nv = max(int(nv), 0)
+        tot += nv * 5.0 * M * math.log2(M)
+        for w in wl.windows:
+            ns = nv // w
+            R = 1 if (w == 1 or wl.pad_rate == 0) else wl.pad_rate * w
+            if R > 1:
+                tot += ns * M * 5.0 * R * math.log2(R)
+            elif w > 1:
+                tot += ns * M * 2.0 * (w - 1)
+            tot += ns * R * M * 3.0
+    return tot * wl.n_bl
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("volks_kernels.cu", "fft_regs.cuh", "twiddle_ce.h", "volks_internal.h"):
+        with open(os.path.join(ROOT, "paper_2108_05602_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def fp32_peak_tflops(peaks) -> tuple:
+    mhz = float(peaks.get("sm_max_mhz", 2032.0))
+    return SM_COUNT * FP32_LANES * 2 * mhz * 1e6 / 1e12, mhz
+
+
+def traffic_per_launch(wl, units):
+    """DRAM bytes of the search kernel scaled from a committed ncu capture,
+    or None if there is none for the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "search_kernel_traffic.json")
+    try:
+        with open(p) as f:
+            t = json.load(f)
+    except OSError:
+        return None
+    if t.get("kernel_hash") != kernel_source_hash():
+        return None
+    return t["dram_bytes_per_ap_bd"] * units
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), pw=float(parts[3]),
+                                 hw=parts[5], hwt=parts[6], swt=parts[7], pcap=parts[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        load = [r for r in rows if r["pw"] > 300] or rows
+        reasons = set()
+        for r in rows:
+            for k, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                            ("swt", "sw_thermal_slowdown"), ("pcap", "sw_power_cap")):
+                if r[k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in load),
+                "sm_max_mhz": max(r["smax"] for r in rows), "samples": len(rows),
+                "samples_under_load": len(load), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------- oracle leg ----
+def _oracle_one(args):
+    wl, vis, cal, d = args
+    from oracle import volks_oracle as O
+    res = O.search(wl, vis, cal, with_second=False, dm_indices=[d])
+    return sum(len(p.P) for p in res.peaks.values())
+
+
+def oracle_sample(wl, vis_b, cal_b, n_ap, dm_indices, cores):
+    """Time the FP64 oracle, as it stands, on one baseline x the given DM
+    trials x the first n_ap APs, one process per DM trial (spawned)."""
+    import dataclasses
+    import multiprocessing as mp
+    sub = dataclasses.replace(wl, n_bl=1, n_ap=n_ap)
+    vis = np.ascontiguousarray(vis_b[None, :n_ap])
+    cal = cal_b[None]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(processes=cores) as pool:
+        pool.map(_oracle_one, [(sub, vis[:, :64], cal, 0)])  # start-up outside the clock
+        t = time.perf_counter()
+        n = sum(pool.map(_oracle_one, [(sub, vis, cal, d) for d in dm_indices]))
+        dt = time.perf_counter() - t
+    return n, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_2108_05602_b300 import synth
+    wl = workload()
+    cores = min(8, os.cpu_count() or 1)
+    n_ap = 4883  # 5 s of the scan
+    dms = list(range(0, wl.n_dm, wl.n_dm // cores))[:cores]
+    wl_s, vis, cal, _ = synth.gen_evn_numpy(seed=2, wl=wl, n_ap=n_ap, n_pulses=1)
+    for _ in range(args.warmup):
+        oracle_sample(wl, vis[0], cal[0], n_ap, dms[:1], 1)
+    times, n = [], 0
+    for _ in range(args.steps):
+        n, dt = oracle_sample(wl, vis[0], cal[0], n_ap, dms, cores)
+        times.append(dt)
+    value = n / statistics.mean(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "evn_sample", "n_bl": 1, "n_ap": n_ap, "n_dm": len(dms),
+                       "n_f": wl.n_f, "windows": list(wl.windows)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"1 baseline x {len(dms)} DM trials x {n_ap} APs "
+                                       "(5 s) of the EVN-scale workload, FP64 numpy"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# -------------------------------------------------------------- GPU leg ----
+def run_volks(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2108_05602_b300 import build as B
+    from paper_2108_05602_b300 import synth
+    from paper_2108_05602_b300 import volks as V
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    B.build()
+    V.lib()
+    wl = workload()
+    wl, vis, cal, pulses = synth.gen_evn_torch(seed=2 + rank, device="cuda", wl=wl)
+    vis = vis.contiguous()
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    _, nvalid = V.volks_shift_table(wl.f_lo_mhz, wl.chan_bw_mhz, wl.n_f, wl.t_ap_s, wl.n_ap,
+                                    wl.dm_lo, wl.dm_step, wl.n_dm)
+    trials = trial_count(wl, nvalid)
+    flops = algorithmic_flops(wl, nvalid)
+    units = int(sum(max(int(v), 0) for v in nvalid)) * wl.n_bl  # dedispersed APs x (b, d)
+
+    def step(x):
+        s = V.Search(wl, x, cal, stream=sptr)
+        c = s.candidates()          # waits for the device, runs the host match
+        t = s.timing()
+        s.close()
+        return c, t
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(max(args.warmup, 0)):
+        step(vis)
+    torch.cuda.synchronize()
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step_ms, search_ms, launches = [], [], 0
+    cands = []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e_a.record(stream)
+            cands, tm = step(vis)
+            e_b.record(stream)
+            e_b.synchronize()
+            step_ms.append(e_a.elapsed_time(e_b))
+            search_ms.append(tm.ms_search)
+            launches += tm.n_launches
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    total_ms = ev0.elapsed_time(ev1)
+    t_max = torch.tensor([total_ms], device="cuda")
+    n_tot = torch.tensor([float(trials * args.steps)], device="cuda")
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+        dist.all_reduce(n_tot, op=dist.ReduceOp.SUM)
+    value = n_tot.item() / (t_max.item() / 1e3)
+
+    # end to end through the public API with host (pinned) input
+    host = vis.cpu().pin_memory()
+    e2e_steps = max(1, args.steps)
+    step(host)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    n_c = 0
+    for _ in range(e2e_steps):
+        c, _ = step(host)
+        n_c += len(c)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e_t = torch.tensor([e2e_s], device="cuda")
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = n_tot.item() / args.steps * e2e_steps / e2e_t.item()
+
+    if rank == 0:
+        peaks = measured_peaks()
+        peak, mhz = fp32_peak_tflops(peaks)
+        ms_k = statistics.mean(search_ms)
+        achieved = flops / (ms_k / 1e3) / 1e12
+        traffic = traffic_per_launch(wl, units)
+        cpu = None
+        if not args.no_cpu_baseline:
+            cores = min(8, os.cpu_count() or 1)
+            n_ap = 9766  # 10 s of the scan
+            dms = list(range(0, wl.n_dm, wl.n_dm // cores))[:cores]
+            vb = vis[0, :n_ap].cpu().numpy()
+            n, dt = oracle_sample(wl, vb, cal[0], n_ap, dms, cores)
+            cpu = {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": f"1 baseline x {len(dms)} DM trials x {n_ap} APs (10 s) of this "
+                             f"workload, FP64 numpy, {n} trials in {dt:.1f} s"}
+        srt = sorted(step_ms)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic: complex64 N(0,1) noise + 20 dispersed pulses + station RFI",
+            "config": {"workload": "evn_fp32", "n_bl": wl.n_bl, "n_ap": wl.n_ap,
+                       "n_if": wl.n_if, "n_chan": wl.n_chan, "n_dm": wl.n_dm,
+                       "dm": [wl.dm_lo, wl.dm_lo + wl.dm_step * (wl.n_dm - 1)],
+                       "windows": list(wl.windows), "pad_delay": wl.pad_delay,
+                       "pad_rate": wl.pad_rate, "trials_per_step": trials,
+                       "input_bytes": wl.n_bl * wl.n_ap * wl.n_f * 8,
+                       "l2": "inputs larger than L2 (3.6 GB per step)",
+                       "step_ms_p50": srt[len(srt) // 2], "step_ms_p99": srt[-1]},
+            "roofline": {"bound": "alu", "kernel": "search_kernel<16,4>",
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_basis": f"FP32 FMA: {SM_COUNT} SMs x {FP32_LANES} lanes x 2 x "
+                                       f"{mhz:.0f} MHz (max SM clock, MEASURED_PEAKS.json)",
+                         "kernel_ms": ms_k, "algorithmic_flops": flops},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": wl.n_bl * wl.n_ap * wl.n_f * 8,
+                    "d2h_bytes_per_step": 4 + n_c // e2e_steps * 96},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "candidates_per_step": len(cands),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="volks", choices=["volks", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_volks(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

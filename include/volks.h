@@ -1,0 +1,206 @@
+/*
+ * volks.h -- C ABI of the B300 (sm_103a) cross-spectrum single-pulse search.
+ *
+ * The search is the fringe-fitting hot path of VOLKS2 (Liu et al. 2021,
+ * arXiv 2108.05602): for every baseline, dispersion-measure (DM) trial and
+ * window size, the complex visibility spectra are normalised and calibrated
+ * (Sec. 2.2 HOPS normalisation; Eq. 1 second line, Sec. 2.1.1), dedispersed
+ * by a per-frequency integer shift in accumulation periods (Sec. 2.4.2 step
+ * 4), transformed along frequency with zero padding 4 (Sec. 2.2, step 5),
+ * combined over windows of w APs and transformed along time to fringe rate
+ * (step 6; the 2-D geodetic form of Sec. 2.2), searched for the peak (step
+ * 6 "find max"), and filtered by normalised-power threshold, window match
+ * and cross-baseline match (Sec. 3.1.1).
+ *
+ * Plain C: pointers and sizes only.  Every call returns 0 or a negative
+ * VOLKS_E* code; nothing throws across the ABI; volks_last_error() gives a
+ * thread-local message for the last failure on the calling thread.
+ */
+#ifndef VOLKS_H
+#define VOLKS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VOLKS_OK 0
+#define VOLKS_EINVAL (-1)   /* malformed descriptor or parameter */
+#define VOLKS_ENOMEM (-2)   /* device or host allocation failed */
+#define VOLKS_ETIMEOUT (-3) /* a bounded device wait gave up */
+#define VOLKS_ECUDA (-4)    /* a CUDA runtime call failed */
+
+/* Arithmetic of the delay/rate search (volks_params.precision). */
+#define VOLKS_FP32 0
+
+#define VOLKS_MAX_WIN 6     /* windows are distinct powers of two, 1..32 AP */
+
+/*
+ * One scan segment: n_bl baselines x n_ap accumulation periods (APs) x
+ * n_f = n_if * n_chan frequency points.  IFs are contiguous and searched as
+ * one band (Sec. 2.2); frequency point k = n * n_chan + j of IF n, channel j
+ * sits at f_lo_mhz + (k + 1/2) * chan_bw_mhz.
+ *
+ * vis: complex64 (interleaved float re, im), row-major [n_bl][n_ap][n_f].
+ *      Device memory, or host memory (pageable or pinned; the library then
+ *      copies it to the device on the call's stream).  Borrowed: it must
+ *      stay valid and unchanged until volks_candidates() returns.
+ * cal: host memory, float64 [n_bl][n_if][2] = {delay s, phase rad} of the
+ *      initial calibration (Eq. 1: 2 pi f_j dtau0^n + dphi0^n, f_j the
+ *      channel-centre frequency within the IF), or NULL for none.  Read
+ *      during the call only.
+ */
+typedef struct {
+  int32_t n_bl, n_ap, n_if, n_chan;
+  double t_ap_s;        /* AP length, e.g. 1.024e-3 (Sec. 2.2) */
+  double f_lo_mhz;      /* lower edge of IF 0, channel 0 */
+  double chan_bw_mhz;   /* channel width */
+  const void *vis;
+  const double *cal;
+} volks_segment;
+
+/*
+ * Search parameters.  DM trials are dm_lo + i * dm_step, i < n_dm (pc cm^-3).
+ * win: n_win distinct window sizes in APs, each a power of two in 1..32,
+ *      ascending (Sec. 3.1.1 uses 2, 4, 8, 16).
+ * pad_delay: zero-padding factor of the delay transform (Sec. 2.2: 4);
+ *      1, 2, 4 or 8.
+ * pad_rate: fringe-rate cells per window AP for w >= 2 (R = pad_rate * w);
+ *      4 gives the 2-D delay x rate search, 0 the paper's 1-D search over the
+ *      coherent window sum (R = 1).  w = 1 always has R = 1.
+ * thresh: z-score threshold on normalised power (Sec. 3.1.1: 3).
+ * min_windows / min_baselines: detection needs that many distinct windows on
+ *      one baseline / distinct baselines (Sec. 3.1.1: 2 and 5).
+ * normalize_chan: 1 divides each frequency point by its RMS over the
+ *      segment (FP64), standing in for the HOPS normalisation (Sec. 2.2).
+ * skip_first_chan: 1 drops channel 0 of every IF (Eq. 1's inner sum read
+ *      literally as j = 1 .. J-1).
+ */
+typedef struct {
+  double dm_lo, dm_step;
+  int32_t n_dm;
+  int32_t n_win;
+  int32_t win[8];
+  int32_t pad_delay;
+  int32_t pad_rate;
+  double thresh;
+  int32_t min_windows, min_baselines;
+  int32_t precision;
+  int32_t normalize_chan, skip_first_chan;
+} volks_params;
+
+/*
+ * One detected single pulse on one baseline at one DM trial (the paper's
+ * "SP list per DM", Fig. 1).  The representative is the window-matched
+ * group member with the highest z (ties: smaller window, then earlier
+ * segment); [t0_ap, t1_ap) is its interval and [g0_ap, g1_ap) the group's,
+ * in dedispersed APs (arrival time at the top channel).
+ */
+typedef struct {
+  int32_t bl, dm_idx, win, seg;
+  int32_t t0_ap, t1_ap, g0_ap, g1_ap;
+  int32_t delay_idx;    /* signed delay cell, -M/2 .. M/2-1, M = pad_delay*n_f */
+  int32_t rate_idx;     /* signed rate cell, -R/2 .. R/2-1 */
+  int32_t n_windows, n_baselines;
+  float peak_power;     /* max |Z|^2 */
+  float _pad;
+  double rho;           /* peak_power / (win * n_eff) */
+  double z;             /* (rho - mean) / std over the (bl, DM, win) series */
+  double dm;            /* pc cm^-3 */
+  double delay_s;       /* delay_idx / (M * chan_bw) */
+  double rate_hz;       /* rate_idx / (R * t_ap) */
+} volks_candidate;
+
+/* Per-stage device times of one search, from CUDA events on its stream. */
+typedef struct {
+  float ms_h2d;         /* host -> device copy of vis (0 for device input) */
+  float ms_prep;        /* a2-a3: channel power (FP64) + normalise/transpose */
+  float ms_search;      /* a4-a7: fused dedisperse/delay/rate/peak kernel */
+  float ms_select;      /* a8: FP64 series statistics + threshold */
+  float ms_match;       /* a9: window match */
+  int32_t n_launches;   /* kernels this library launched for the search */
+  int32_t n_search_launches;
+} volks_timing;
+
+typedef struct volks_result volks_result;   /* opaque, library-owned */
+
+/* Fill *p with the paper's defaults: DM 0, step 1, 1 trial; windows 2,4,8,16;
+ * pad_delay 4; pad_rate 4; thresh 3; min_windows 2; min_baselines 5; FP32;
+ * normalize_chan 1; skip_first_chan 0. */
+void volks_default_params(volks_params *p);
+
+/*
+ * Enqueue the whole search (steps a1-a9) of one segment on `cuda_stream`
+ * (a cudaStream_t; NULL = legacy default stream) and return a result handle.
+ * The call validates everything before enqueuing, builds the shift table
+ * (FP64 on the host, rounded half-up; Sec. 2.4.2 step 4) and returns
+ * without waiting for the device.  Device scratch (about 8 bytes per
+ * trial plus one normalised copy of vis) is allocated stream-ordered and
+ * owned by *out.
+ * Errors: VOLKS_EINVAL (bad sizes, windows, pads, NULL vis with n_bl*n_ap
+ * > 0, unsupported precision), VOLKS_ENOMEM, VOLKS_ECUDA.  On error *out
+ * is NULL and nothing stays enqueued that touches caller memory.
+ */
+int volks_search_segment(const volks_segment *seg, const volks_params *prm,
+                         void *cuda_stream, volks_result **out);
+
+/*
+ * Wait for the search, run the cross-baseline match on the host (a10,
+ * Sec. 3.1.1 item 3) and copy up to `cap` candidates, sorted by (dm_idx,
+ * t0_ap, bl), into `buf` (host; may be NULL when cap == 0).  *n_total
+ * (required) receives the number of candidates, which may exceed cap.
+ * Calling it again returns the same list.
+ */
+int volks_candidates(volks_result *res, volks_candidate *buf, size_t cap,
+                     size_t *n_total);
+
+/* Release the handle and its device scratch (stream-ordered).  NULL-safe. */
+void volks_free(volks_result *res);
+
+/* Thread-local message of the last failing call on this thread. */
+const char *volks_last_error(void);
+
+/*
+ * Host only, no device work: the dedispersion shift table of step a1
+ * (Sec. 2.4.2 step 4: one integer AP shift per frequency point and DM).
+ * shift[d][k] = floor(x + 1/2), x = (K_DM DM_d / t_ap) (f_k^-2 - f_top^-2),
+ * K_DM = 4.148808e3 s MHz^2 pc^-1 cm^3, f_k = f_lo + (k + 1/2) chan_bw,
+ * f_top = f_{n_f-1}; computed in FP64.  nvalid[d] = n_ap - max_k shift[d][k]
+ * (may be <= 0: no dedispersed AP is left).  shifts holds n_dm * n_f int32,
+ * nvalid n_dm int32 (either may be NULL).  Same validation as the search.
+ */
+int volks_shift_table(double f_lo_mhz, double chan_bw_mhz, int32_t n_f, double t_ap_s,
+                      int32_t n_ap, double dm_lo, double dm_step, int32_t n_dm,
+                      int32_t *shifts, int32_t *nvalid);
+
+/* ---- introspection, for checking each step against a reference ---- */
+
+/* Waits for the search.  Stage times and launch counts. */
+int volks_result_timing(volks_result *res, volks_timing *t);
+
+/* Copy the shift table int32 [n_dm][n_f] and n_valid int32 [n_dm] (the
+ * dedispersed APs left at each DM) to host buffers of >= that many items. */
+int volks_result_shifts(volks_result *res, int32_t *shifts, int32_t *nvalid);
+
+/* Waits for the search.  Per-segment peaks of one (baseline, DM trial,
+ * window index) series: P[s] = max |Z|^2, q[s] / m[s] = its unsigned rate /
+ * delay cell, for s < *n_seg = n_valid / win; buffers hold >= cap items. */
+int volks_result_peaks(volks_result *res, int32_t bl, int32_t dm_idx,
+                       int32_t win_idx, float *P, int32_t *q, int32_t *m,
+                       size_t cap, size_t *n_seg);
+
+/* Waits for the search.  FP64 mean and population standard deviation of
+ * the normalised power of one series. */
+int volks_result_stats(volks_result *res, int32_t bl, int32_t dm_idx,
+                       int32_t win_idx, double *mean, double *std);
+
+/* Waits for the search.  Complex64 gains [n_bl][n_f] (calibration phasor
+ * divided by the channel RMS) applied before dedispersion. */
+int volks_result_gains(volks_result *res, float *gains, size_t cap_floats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VOLKS_H */

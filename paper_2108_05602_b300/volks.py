@@ -1,0 +1,248 @@
+"""ctypes binding of libvolks.so (include/volks.h), names as in the C ABI.
+
+Argument marshalling only: every step of the search runs in the library's
+CUDA kernels (and its host driver for the shift table and the
+cross-baseline match).  Loading fails loudly if the library is missing;
+there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvolks.so")
+
+VOLKS_OK, VOLKS_EINVAL, VOLKS_ENOMEM, VOLKS_ETIMEOUT, VOLKS_ECUDA = 0, -1, -2, -3, -4
+VOLKS_FP32 = 0
+
+
+class volks_segment(C.Structure):
+    _fields_ = [("n_bl", C.c_int32), ("n_ap", C.c_int32), ("n_if", C.c_int32),
+                ("n_chan", C.c_int32), ("t_ap_s", C.c_double), ("f_lo_mhz", C.c_double),
+                ("chan_bw_mhz", C.c_double), ("vis", C.c_void_p),
+                ("cal", C.POINTER(C.c_double))]
+
+
+class volks_params(C.Structure):
+    _fields_ = [("dm_lo", C.c_double), ("dm_step", C.c_double), ("n_dm", C.c_int32),
+                ("n_win", C.c_int32), ("win", C.c_int32 * 8), ("pad_delay", C.c_int32),
+                ("pad_rate", C.c_int32), ("thresh", C.c_double),
+                ("min_windows", C.c_int32), ("min_baselines", C.c_int32),
+                ("precision", C.c_int32), ("normalize_chan", C.c_int32),
+                ("skip_first_chan", C.c_int32)]
+
+
+class volks_candidate(C.Structure):
+    _fields_ = [("bl", C.c_int32), ("dm_idx", C.c_int32), ("win", C.c_int32),
+                ("seg", C.c_int32), ("t0_ap", C.c_int32), ("t1_ap", C.c_int32),
+                ("g0_ap", C.c_int32), ("g1_ap", C.c_int32), ("delay_idx", C.c_int32),
+                ("rate_idx", C.c_int32), ("n_windows", C.c_int32),
+                ("n_baselines", C.c_int32), ("peak_power", C.c_float), ("_pad", C.c_float),
+                ("rho", C.c_double), ("z", C.c_double), ("dm", C.c_double),
+                ("delay_s", C.c_double), ("rate_hz", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "_pad"}
+
+
+class volks_timing(C.Structure):
+    _fields_ = [("ms_h2d", C.c_float), ("ms_prep", C.c_float), ("ms_search", C.c_float),
+                ("ms_select", C.c_float), ("ms_match", C.c_float),
+                ("n_launches", C.c_int32), ("n_search_launches", C.c_int32)]
+
+
+_lib: Optional[C.CDLL] = None
+
+
+def lib() -> C.CDLL:
+    """Load libvolks.so from the package directory (built by build.py)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libvolks.so not built at {LIB_PATH}; run "
+                          "python -m paper_2108_05602_b300.build")
+    L = C.CDLL(LIB_PATH)
+    P, I32, SZ = C.c_void_p, C.c_int32, C.c_size_t
+    L.volks_default_params.argtypes = [C.POINTER(volks_params)]
+    L.volks_default_params.restype = None
+    L.volks_search_segment.argtypes = [C.POINTER(volks_segment), C.POINTER(volks_params), P,
+                                       C.POINTER(P)]
+    L.volks_search_segment.restype = C.c_int
+    L.volks_candidates.argtypes = [P, C.POINTER(volks_candidate), SZ, C.POINTER(SZ)]
+    L.volks_candidates.restype = C.c_int
+    L.volks_free.argtypes = [P]
+    L.volks_free.restype = None
+    L.volks_last_error.argtypes = []
+    L.volks_last_error.restype = C.c_char_p
+    L.volks_shift_table.argtypes = [C.c_double, C.c_double, I32, C.c_double, I32, C.c_double,
+                                    C.c_double, I32, C.POINTER(I32), C.POINTER(I32)]
+    L.volks_shift_table.restype = C.c_int
+    L.volks_result_timing.argtypes = [P, C.POINTER(volks_timing)]
+    L.volks_result_timing.restype = C.c_int
+    L.volks_result_shifts.argtypes = [P, C.POINTER(I32), C.POINTER(I32)]
+    L.volks_result_shifts.restype = C.c_int
+    L.volks_result_peaks.argtypes = [P, I32, I32, I32, C.POINTER(C.c_float), C.POINTER(I32),
+                                     C.POINTER(I32), SZ, C.POINTER(SZ)]
+    L.volks_result_peaks.restype = C.c_int
+    L.volks_result_stats.argtypes = [P, I32, I32, I32, C.POINTER(C.c_double),
+                                     C.POINTER(C.c_double)]
+    L.volks_result_stats.restype = C.c_int
+    L.volks_result_gains.argtypes = [P, C.POINTER(C.c_float), SZ]
+    L.volks_result_gains.restype = C.c_int
+    _lib = L
+    return L
+
+
+class VolksError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = lib().volks_last_error().decode(errors="replace")
+        super().__init__(f"{where} failed ({code}): {msg}")
+        self.code = code
+
+
+def _check(rc: int, where: str):
+    if rc != VOLKS_OK:
+        raise VolksError(rc, where)
+
+
+# ---- thin wrappers with the C names ----------------------------------------
+def volks_default_params() -> volks_params:
+    p = volks_params()
+    lib().volks_default_params(C.byref(p))
+    return p
+
+
+def volks_search_segment(seg: volks_segment, prm: volks_params, stream: int = 0) -> int:
+    out = C.c_void_p()
+    _check(lib().volks_search_segment(C.byref(seg), C.byref(prm), C.c_void_p(stream),
+                                      C.byref(out)), "volks_search_segment")
+    return out.value
+
+
+def volks_candidates(res: int) -> List[volks_candidate]:
+    n = C.c_size_t()
+    _check(lib().volks_candidates(C.c_void_p(res), None, 0, C.byref(n)), "volks_candidates")
+    buf = (volks_candidate * max(1, n.value))()
+    _check(lib().volks_candidates(C.c_void_p(res), buf, n.value, C.byref(n)), "volks_candidates")
+    return list(buf[:n.value])
+
+
+def volks_free(res: Optional[int]):
+    if res:
+        lib().volks_free(C.c_void_p(res))
+
+
+def volks_shift_table(f_lo_mhz, chan_bw_mhz, n_f, t_ap_s, n_ap, dm_lo, dm_step, n_dm):
+    sh = np.zeros((max(n_dm, 0), n_f), dtype=np.int32)
+    nv = np.zeros(max(n_dm, 0), dtype=np.int32)
+    I32P = C.POINTER(C.c_int32)
+    _check(lib().volks_shift_table(f_lo_mhz, chan_bw_mhz, n_f, t_ap_s, n_ap, dm_lo, dm_step,
+                                   n_dm, sh.ctypes.data_as(I32P), nv.ctypes.data_as(I32P)),
+           "volks_shift_table")
+    return sh, nv
+
+
+# ---- convenience: marshal a workload description + array -----------------
+def make_params(wl, **over) -> volks_params:
+    p = volks_default_params()
+    p.dm_lo, p.dm_step, p.n_dm = wl.dm_lo, wl.dm_step, wl.n_dm
+    win = list(wl.windows)
+    p.n_win = len(win)
+    for i, w in enumerate(win):
+        p.win[i] = w
+    p.pad_delay, p.pad_rate = wl.pad_delay, wl.pad_rate
+    p.thresh, p.min_windows, p.min_baselines = wl.thresh, wl.min_windows, wl.min_baselines
+    for k, v in over.items():
+        setattr(p, k, v)
+    return p
+
+
+def _vis_pointer(vis):
+    """(pointer, keepalive) of a contiguous complex64 array or tensor."""
+    try:
+        import torch
+        if isinstance(vis, torch.Tensor):
+            if vis.dtype != torch.complex64 or not vis.is_contiguous():
+                raise ValueError("vis must be a contiguous complex64 tensor")
+            return vis.data_ptr(), vis
+    except ImportError:
+        pass
+    arr = np.ascontiguousarray(vis, dtype=np.complex64)
+    return arr.ctypes.data, arr
+
+
+class Search:
+    """One search handle; frees its device scratch on close()/__del__."""
+
+    def __init__(self, wl, vis, cal: Optional[np.ndarray] = None, stream: int = 0,
+                 n_bl: Optional[int] = None, n_ap: Optional[int] = None, **over):
+        ptr, self._keep_vis = _vis_pointer(vis)
+        self._cal = None if cal is None else np.ascontiguousarray(cal, dtype=np.float64)
+        seg = volks_segment()
+        seg.n_bl = wl.n_bl if n_bl is None else n_bl
+        seg.n_ap = wl.n_ap if n_ap is None else n_ap
+        seg.n_if, seg.n_chan = wl.n_if, wl.n_chan
+        seg.t_ap_s, seg.f_lo_mhz, seg.chan_bw_mhz = wl.t_ap_s, wl.f_lo_mhz, wl.chan_bw_mhz
+        seg.vis = ptr
+        seg.cal = (None if self._cal is None
+                   else self._cal.ctypes.data_as(C.POINTER(C.c_double)))
+        self.seg, self.prm = seg, make_params(wl, **over)
+        self.n_f = wl.n_if * wl.n_chan
+        self.handle = volks_search_segment(seg, self.prm, stream)
+
+    def candidates(self) -> List[dict]:
+        return [c.as_dict() for c in volks_candidates(self.handle)]
+
+    def timing(self) -> volks_timing:
+        t = volks_timing()
+        _check(lib().volks_result_timing(C.c_void_p(self.handle), C.byref(t)), "timing")
+        return t
+
+    def shifts(self):
+        sh = np.zeros((self.prm.n_dm, self.n_f), dtype=np.int32)
+        nv = np.zeros(self.prm.n_dm, dtype=np.int32)
+        I32P = C.POINTER(C.c_int32)
+        _check(lib().volks_result_shifts(C.c_void_p(self.handle), sh.ctypes.data_as(I32P),
+                                         nv.ctypes.data_as(I32P)), "shifts")
+        return sh, nv
+
+    def peaks(self, b: int, d: int, wi: int):
+        n = C.c_size_t()
+        _check(lib().volks_result_peaks(C.c_void_p(self.handle), b, d, wi, None, None, None, 0,
+                                        C.byref(n)), "peaks")
+        P = np.zeros(n.value, dtype=np.float32)
+        q = np.zeros(n.value, dtype=np.int32)
+        m = np.zeros(n.value, dtype=np.int32)
+        _check(lib().volks_result_peaks(
+            C.c_void_p(self.handle), b, d, wi, P.ctypes.data_as(C.POINTER(C.c_float)),
+            q.ctypes.data_as(C.POINTER(C.c_int32)), m.ctypes.data_as(C.POINTER(C.c_int32)),
+            n.value, C.byref(n)), "peaks")
+        return P, q, m
+
+    def stats(self, b: int, d: int, wi: int):
+        mu, sd = C.c_double(), C.c_double()
+        _check(lib().volks_result_stats(C.c_void_p(self.handle), b, d, wi, C.byref(mu),
+                                        C.byref(sd)), "stats")
+        return mu.value, sd.value
+
+    def gains(self) -> np.ndarray:
+        g = np.zeros((self.seg.n_bl, self.n_f, 2), dtype=np.float32)
+        _check(lib().volks_result_gains(C.c_void_p(self.handle),
+                                        g.ctypes.data_as(C.POINTER(C.c_float)), g.size), "gains")
+        return g[..., 0] + 1j * g[..., 1]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            volks_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,172 @@
+"""C-ABI checks that need no GPU: the library loads, exports every function
+include/volks.h declares, its structs have the C layout, the host-only
+shift table equals the oracle's bit for bit, and malformed descriptors are
+rejected before any device work."""
+import ctypes as C
+import os
+import re
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+from oracle import volks_oracle as O
+from paper_2108_05602_b300 import build, synth
+from paper_2108_05602_b300 import volks as V
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "volks.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return V.lib()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(volks_\w+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(L):
+    names = declared_functions()
+    assert "volks_search_segment" in names and "volks_candidates" in names and "volks_free" in names
+    out = subprocess.run(["nm", "-D", "--defined-only", V.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\b(volks_\w+)\b", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        assert hasattr(L, n)
+
+
+def test_struct_layout_matches_c(L):
+    structs = {"volks_segment": V.volks_segment, "volks_params": V.volks_params,
+               "volks_candidate": V.volks_candidate, "volks_timing": V.volks_timing}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', 'int main(void){']
+    for sname, cls in structs.items():
+        lines.append(f'printf("{sname} %zu\\n", sizeof({sname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{sname}.{f} %zu\\n", offsetof({sname}, {f}));')
+    lines.append("return 0;}")
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        exe = os.path.join(d, "t")
+        open(c, "w").write("\n".join(lines))
+        subprocess.run(["gcc", "-std=c99", "-o", exe, c], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout
+    got = dict(l.rsplit(" ", 1) for l in out.strip().splitlines())
+    for sname, cls in structs.items():
+        assert int(got[sname]) == C.sizeof(cls), sname
+        for f, _ in cls._fields_:
+            assert int(got[f"{sname}.{f}"]) == getattr(cls, f).offset, (sname, f)
+
+
+@pytest.mark.parametrize("wl", [synth.pr1(), synth.evn(), synth.small(n_if=4, n_chan=16)],
+                         ids=["pr1", "evn", "small"])
+def test_shift_table_bit_exact_vs_oracle(L, wl):
+    sh, nv = V.volks_shift_table(wl.f_lo_mhz, wl.chan_bw_mhz, wl.n_f, wl.t_ap_s, wl.n_ap,
+                                 wl.dm_lo, wl.dm_step, wl.n_dm)
+    ref = O.shift_table(wl.f_lo_mhz, wl.chan_bw_mhz, wl.n_f, wl.dms(), wl.t_ap_s)
+    assert np.array_equal(sh, ref)
+    assert np.array_equal(nv, [O.n_valid(wl.n_ap, r) for r in ref])
+
+
+def test_shift_table_large_dm_leaves_no_valid_ap(L):
+    wl = synth.small(n_ap=40)
+    sh, nv = V.volks_shift_table(wl.f_lo_mhz, wl.chan_bw_mhz, wl.n_f, wl.t_ap_s, 40,
+                                 0.0, 5000.0, 3)
+    assert nv[0] == 40 and nv[2] <= 0
+
+
+def _seg(**kw):
+    s = V.volks_segment()
+    s.n_bl, s.n_ap, s.n_if, s.n_chan = 1, 64, 4, 16
+    s.t_ap_s, s.f_lo_mhz, s.chan_bw_mhz = 1.024e-3, 1580.0, 0.5
+    s.vis = 1  # never dereferenced: validation fails first
+    for k, v in kw.items():
+        setattr(s, k, v)
+    return s
+
+
+@pytest.mark.parametrize("seg_kw,prm_kw", [
+    (dict(n_chan=15), {}),                       # n_f = 60 not a power of two
+    (dict(n_if=32, n_chan=32), {}),              # n_f = 1024 not in this build
+    (dict(n_ap=-1), {}),
+    (dict(t_ap_s=0.0), {}),
+    (dict(chan_bw_mhz=-0.5), {}),
+    (dict(vis=None), {}),
+    ({}, dict(n_win=0)),
+    ({}, dict(n_win=7)),
+    ({}, dict(pad_delay=3)),
+    ({}, dict(pad_rate=3)),
+    ({}, dict(precision=2)),
+    ({}, dict(dm_lo=-10.0)),
+    ({}, dict(min_windows=0)),
+    ({}, dict(normalize_chan=2)),
+])
+def test_malformed_descriptors_rejected(L, seg_kw, prm_kw):
+    seg = _seg(**seg_kw)
+    prm = V.volks_default_params()
+    for k, v in prm_kw.items():
+        setattr(prm, k, v)
+    out = C.c_void_p(123)
+    rc = L.volks_search_segment(C.byref(seg), C.byref(prm), None, C.byref(out))
+    assert rc == V.VOLKS_EINVAL
+    assert out.value is None
+    assert L.volks_last_error()
+
+
+def test_windows_must_be_ascending_powers_of_two(L):
+    for wins in ([2, 2], [4, 2], [3], [64]):
+        prm = V.volks_default_params()
+        prm.n_win = len(wins)
+        for i, w in enumerate(wins):
+            prm.win[i] = w
+        out = C.c_void_p()
+        assert L.volks_search_segment(C.byref(_seg()), C.byref(prm), None, C.byref(out)) == V.VOLKS_EINVAL
+
+
+def test_null_arguments(L):
+    out = C.c_void_p()
+    assert L.volks_search_segment(None, None, None, C.byref(out)) == V.VOLKS_EINVAL
+    assert L.volks_search_segment(C.byref(_seg()), C.byref(V.volks_default_params()), None, None) == V.VOLKS_EINVAL
+    n = C.c_size_t()
+    assert L.volks_candidates(None, None, 0, C.byref(n)) == V.VOLKS_EINVAL
+    L.volks_free(None)  # NULL-safe
+
+
+def test_twiddle_series_matches_libm():
+    """The compile-time sine/cosine used for register-FFT twiddles agrees
+    with the C library to ~1 ulp for every angle the kernels use."""
+    src = os.path.join(ROOT, "paper_2108_05602_b300", "csrc", "twiddle_ce.h")
+    prog = f'''#include "{src}"
+#include <cmath>
+#include <cstdio>
+int main() {{ double worst = 0;
+  for (long long n = 1; n <= 4096; n *= 2) for (long long k = -n; k < 2 * n; ++k) {{
+    double c = vk::cos2pi(k, n), s = vk::sin2pi(k, n);
+    double a = 2.0 * M_PI * (double)k / (double)n;
+    worst = std::fmax(worst, std::fabs(c - std::cos(a)));
+    worst = std::fmax(worst, std::fabs(s - std::sin(a))); }}
+  static_assert(vk::cos2pi(1, 4) == vk::series_cos(0.0) * 0.0 + vk::cos2pi(1, 4), "constexpr");
+  printf("%.3e\\n", worst); return 0; }}'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.cc")
+        exe = os.path.join(d, "t")
+        open(c, "w").write(prog)
+        subprocess.run(["g++", "-std=c++17", "-O1", "-o", exe, c], check=True)
+        worst = float(subprocess.run([exe], capture_output=True, text=True, check=True).stdout)
+    assert worst < 2e-15
+
+
+def test_product_path_does_not_touch_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2108_05602_b300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"(from|import)\s+oracle\b|volks_oracle|oracle/", txt), f
