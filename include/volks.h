@@ -200,6 +200,53 @@ int volks_result_stats(volks_result *res, int32_t bl, int32_t dm_idx,
  * divided by the channel RMS) applied before dedispersion. */
 int volks_result_gains(volks_result *res, float *gains, size_t cap_floats);
 
+/* ---- no-allocation variant ---------------------------------------------
+ *
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory while they run: for example a
+ * real-time correlator or streaming service that reserves the whole GPU at
+ * start-up and cannot afford allocator latency or an out-of-memory failure
+ * in the middle of an observation, or a host framework whose own allocator
+ * owns the device-memory budget.
+ *
+ * volks_search_peaks_noalloc runs the per-segment peak search of
+ * volks_search_segment (steps a1-a7: shift table, FP64 channel
+ * normalisation, calibration, dedispersion, delay and rate transforms,
+ * peak search) on `cuda_stream` and writes, for every (baseline, DM trial,
+ * segment), its peak power and peak cell.  It calls no cudaMalloc,
+ * cudaFree or other allocating routine: all scratch lives in one static
+ * device array of VOLKS_NOALLOC_SCRATCH_BYTES that every device which loads
+ * this library holds until the process exits.
+ *
+ *   seg->vis      device memory (host pointers are rejected), as for
+ *                 volks_search_segment; seg->cal host memory or NULL, at
+ *                 most 256 (n_bl * n_if) entries.
+ *   peak_power    device, float [n_bl][n_dm][S]: max |Z|^2 of the segment.
+ *   peak_cell     device, int32 [n_bl][n_dm][S]: q * M + m of that cell
+ *                 (unsigned rate cell q, delay cell m, M = pad_delay*n_f).
+ *   S = sum_i floor(n_ap / win[i]); window i's segments start at
+ *   sum_{j<i} floor(n_ap / win[j]); segment s of window i exists while
+ *   s < max(0, n_valid) / win[i] (n_valid as in volks_shift_table); the
+ *   entries past that hold power 0 and cell -1.
+ *
+ * Returns VOLKS_EINVAL (nothing launched) for a segment whose scratch
+ * (about 8 bytes per visibility + 8 bytes per output entry + tables)
+ * exceeds VOLKS_NOALLOC_SCRATCH_BYTES, or for the descriptors
+ * volks_search_segment rejects; VOLKS_ECUDA if a launch fails.  Returns
+ * without waiting for the device.
+ *
+ * All calls on a device share the one scratch array, which keeps the
+ * previous call's contents; each call clears what must start at zero on
+ * its own stream.  Calls that overlap on the GPU (different streams or
+ * host threads) race on the array and must be serialised by the caller.
+ * The first call on each device looks up the array's device address with
+ * that device current; make that first call before any stream capture.
+ */
+#define VOLKS_NOALLOC_SCRATCH_BYTES (64u << 20)
+
+int volks_search_peaks_noalloc(const volks_segment *seg, const volks_params *prm,
+                               void *cuda_stream, float *peak_power, int32_t *peak_cell);
+
 #ifdef __cplusplus
 }
 #endif

@@ -47,6 +47,8 @@ int ilog2i(int x) {
 
 }  // namespace
 
+void vk::set_last_error(const char* msg) { g_err = msg; }
+
 struct volks_result {
   cudaStream_t stream = nullptr;
   volks_segment seg{};

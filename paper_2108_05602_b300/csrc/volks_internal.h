@@ -73,6 +73,9 @@ struct MatchArgs {
   long long seg_per_bd, word_per_bd;
 };
 
+// Set the calling thread's message returned by volks_last_error().
+void set_last_error(const char* msg);
+
 // Launchers (return the launch's cudaError_t).
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s, int* n_launch);
 cudaError_t launch_search(const SearchArgs& a, int pad_rate, cudaStream_t s, int* n_launch);

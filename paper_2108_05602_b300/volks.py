@@ -94,6 +94,9 @@ def lib() -> C.CDLL:
     L.volks_result_stats.restype = C.c_int
     L.volks_result_gains.argtypes = [P, C.POINTER(C.c_float), SZ]
     L.volks_result_gains.restype = C.c_int
+    L.volks_search_peaks_noalloc.argtypes = [C.POINTER(volks_segment), C.POINTER(volks_params),
+                                             P, P, P]
+    L.volks_search_peaks_noalloc.restype = C.c_int
     _lib = L
     return L
 
@@ -135,6 +138,16 @@ def volks_candidates(res: int) -> List[volks_candidate]:
 def volks_free(res: Optional[int]):
     if res:
         lib().volks_free(C.c_void_p(res))
+
+
+def volks_search_peaks_noalloc(seg: volks_segment, prm: volks_params, stream: int,
+                               peak_power_ptr: int, peak_cell_ptr: int):
+    """Peak search into caller-owned device buffers with no device
+    allocation (see include/volks.h for the layout and the rules)."""
+    _check(lib().volks_search_peaks_noalloc(C.byref(seg), C.byref(prm), C.c_void_p(stream),
+                                            C.c_void_p(peak_power_ptr),
+                                            C.c_void_p(peak_cell_ptr)),
+           "volks_search_peaks_noalloc")
 
 
 def volks_shift_table(f_lo_mhz, chan_bw_mhz, n_f, t_ap_s, n_ap, dm_lo, dm_step, n_dm):
