@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <set>
 #include <string>
@@ -113,8 +114,8 @@ int validate(const volks_segment* s, const volks_params* p) {
   if (s->n_bl < 0 || s->n_ap < 0) return fail(VOLKS_EINVAL, "negative n_bl or n_ap");
   if (s->n_if < 1 || s->n_chan < 1) return fail(VOLKS_EINVAL, "n_if and n_chan must be >= 1");
   const long long n_f = (long long)s->n_if * s->n_chan;
-  if (!is_pow2(n_f) || n_f < 64 || n_f > 512)
-    return fail(VOLKS_EINVAL, "n_if*n_chan = %lld: this build supports powers of two 64..512", n_f);
+  if (!is_pow2(n_f) || n_f < 64 || n_f > 2048)
+    return fail(VOLKS_EINVAL, "n_if*n_chan = %lld: this build supports powers of two 64..2048", n_f);
   if (!(std::isfinite(s->t_ap_s) && s->t_ap_s > 0)) return fail(VOLKS_EINVAL, "t_ap_s must be > 0");
   if (!(std::isfinite(s->chan_bw_mhz) && s->chan_bw_mhz > 0))
     return fail(VOLKS_EINVAL, "chan_bw_mhz must be > 0");
@@ -263,7 +264,7 @@ int volks_search_segment(const volks_segment* seg, const volks_params* prm, void
   VK_TRY(cudaEventRecord(r->ev[0], st), "event");
 
   // candidates buffer exists even for an empty search
-  r->cap = (unsigned)std::max<long long>(4096, std::min<long long>(1LL << 22, (long long)n_bl * n_dm * 16));
+  r->cap = (unsigned)std::max<long long>(4096, std::min<long long>(1LL << 24, (long long)n_bl * n_dm * 64));
   VK_TRY(dalloc(&r->d_cand, r->cap, st), "alloc candidates");
   VK_TRY(dalloc(&r->d_count, 1, st), "alloc count");
   VK_TRY(cudaMemsetAsync(r->d_count, 0, sizeof(unsigned int), st), "memset count");
@@ -373,6 +374,8 @@ int volks_search_segment(const volks_segment* seg, const volks_params* prm, void
   for (int i = 0; i < n_win; ++i) sa.win_off[r->win_log[i]] = r->win_off[i];
   sa.seg_per_bd = r->seg_per_bd;
   sa.n_tiles = r->n_tiles;
+  sa.fold = 1;  // measured: one 512-thread CTA beats two folded 256-thread CTAs at n_f = 512
+  if (const char* f = std::getenv("VOLKS_SEARCH_FOLD")) sa.fold = std::atoi(f);
   const int before = r->n_launch;
   VK_TRY(vk::launch_search(sa, prm->pad_rate, st, &r->n_launch), "search kernel");
   r->n_search_launch = r->n_launch - before;

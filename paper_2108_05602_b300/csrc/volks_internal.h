@@ -43,6 +43,7 @@ struct SearchArgs {
   int win_off[kMaxWinLog + 1];     // segment offset of window 2^l inside a (b, d) block
   long long seg_per_bd;
   int n_tiles;
+  int fold;                        // n_f = 512 only: 1 = one 512-thread CTA, else two 256-thread CTAs
 };
 
 struct SelectArgs {

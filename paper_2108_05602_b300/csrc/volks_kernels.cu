@@ -103,6 +103,25 @@ cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s, int* n_launch) {
 }
 
 // ============================================================ search ====
+// Arg-max over cells LO .. LO+LEN-1 by a balanced tree (depth log2 LEN, so
+// the compare/select chain does not serialise): the right half wins only if
+// strictly larger, which keeps the lowest index on exact ties.
+template <int LO, int LEN, class F>
+__device__ __forceinline__ void argmax_tree(const F& pw, float& v, uint32_t& q) {
+  if constexpr (LEN == 1) {
+    v = pw(std::integral_constant<int, LO>{});
+    q = LO;
+  } else {
+    float v1, v2;
+    uint32_t q1, q2;
+    argmax_tree<LO, LEN / 2>(pw, v1, q1);
+    argmax_tree<LO + LEN / 2, LEN / 2>(pw, v2, q2);
+    const bool right = v2 > v1;
+    v = right ? v2 : v1;
+    q = right ? q2 : q1;
+  }
+}
+
 // Rate transform, |Z|^2 and arg-max of every window-W segment of the tile
 // for the delay column this thread owns.  Per segment the warp's best
 // (power, lowest linear cell) goes to slot[(slot0 + s) * N1 + warp].
@@ -124,6 +143,18 @@ __device__ __forceinline__ void rate_window(const float2* __restrict__ S, int c,
       static_for<1, W>([&](auto u) { z = cadd(z, col[decltype(u)::value * LD]); });
       best = cabs2(z);
       bq = 0;
+    } else if constexpr (W == 2 && R == 8) {
+      // |y0 + y1 W_8^q|^2 = r0 + 2 Re(r1 W_8^q), r0 = |y0|^2 + |y1|^2,
+      // r1 = y1 conj(y0): the power spectrum is the DFT of the lag products.
+      const float2 y0 = col[0], y1 = col[LD];
+      const float r0 = fmaf(y1.y, y1.y, fmaf(y1.x, y1.x, cabs2(y0)));
+      const float rx = fmaf(y1.y, y0.y, y1.x * y0.x);
+      const float ry = fmaf(y1.y, y0.x, -(y1.x * y0.y));
+      constexpr float kS2 = Tw<8, 1>::re * 2.0f;   // sqrt(2)
+      const float a = rx + rx, bb = ry + ry;
+      const float cc = kS2 * (rx + ry), dd = kS2 * (ry - rx);
+      const float P[8] = {r0 + a, r0 + cc, r0 + bb, r0 + dd, r0 - a, r0 - cc, r0 - bb, r0 - dd};
+      argmax_tree<0, 8>([&](auto qq) { return P[decltype(qq)::value]; }, best, bq);
     } else {
       best = -1.f;
       bq = 0;
@@ -137,16 +168,10 @@ __device__ __forceinline__ void rate_window(const float2* __restrict__ S, int c,
           y[U] = twiddle<R, U * RHO>(col[U * LD]);
         });
         fft_dif<W>(y);
-        float vb = cabs2(y[0]);
-        uint32_t vq = 0;
-        static_for<1, W>([&](auto qq) {
-          constexpr int Q = decltype(qq)::value;
-          const float p = cabs2(y[bitrev(Q, ilog2(W))]);
-          if (p > vb) {
-            vb = p;
-            vq = Q;
-          }
-        });
+        float vb;
+        uint32_t vq;
+        argmax_tree<0, W>([&](auto qq) { return cabs2(y[bitrev(decltype(qq)::value, ilog2(W))]); },
+                          vb, vq);
         const uint32_t q = PADR * vq + RHO;
         if (vb > best || (vb == best && q < bq)) {
           best = vb;
@@ -162,16 +187,19 @@ __device__ __forceinline__ void rate_window(const float2* __restrict__ S, int c,
   }
 }
 
-// One CTA = (baseline b, DM trial d, 32-AP tile, delay residue r).  The
-// residue pass computes the delay cells m = pad_delay * c + r (c < N) as an
-// N-point FFT of the pre-twiddled spectrum x[k] W_M^{k r} (zero padding by
-// pad_delay means the M-point transform splits into pad_delay such FFTs).
-// N = 32 * N1 = n_f; the CTA has N threads.
-//   stage 0  lane = AP, warp owns k0 = warp*KPW + j: x = xn[k][t + shift_k]
+// One CTA = (baseline b, DM trial d, 32-AP tile, delay residue r).  Zero
+// padding by pad_delay, with the band folded FOLD times, splits the M-point
+// delay transform (M = pad_delay * n_f) into P = pad_delay * FOLD
+// independent N-point FFTs, N = n_f / FOLD:
+//   Y[P c + r] = sum_{k<N} W_M^{k r} (sum_{f<FOLD} X[k + N f] W_P^{f r}) W_N^{k c},
+// so a CTA computes the delay cells m = P c + r (c < N) of its residue r.
+// N = 32 * N1; the CTA has N threads.
+//   stage 0  lane = AP, warp owns k0 = warp*KPW + j: gather xn[k][t + shift_k],
+//            fold and pre-twiddle
 //   stage 1  N1-point FFTs over k1 (k = k0 + 32 k1), twiddle W_N^{k0 m1}
 //   stage 2  lane = AP, warp = m1: 32-point FFT over k0 -> Y[m1 + N1 m2]
 //   stage 3  thread = delay column c: rate FFTs over the tile's APs
-template <int N1, int PADR>
+template <int N1, int PADR, int FOLD>
 __global__ void __launch_bounds__(32 * N1, 16 / N1) search_kernel(const SearchArgs a, int b_base) {
   constexpr int N = 32 * N1;
   constexpr int KPW = 32 / N1;
@@ -181,9 +209,10 @@ __global__ void __launch_bounds__(32 * N1, 16 / N1) search_kernel(const SearchAr
   uint2* slot = reinterpret_cast<uint2*>(sm + 32 * LD);
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int P = a.pad_delay * FOLD;
   long long bid = blockIdx.x;
-  const int r = (int)(bid % a.pad_delay);
-  bid /= a.pad_delay;
+  const int r = (int)(bid % P);
+  bid /= P;
   const int d = (int)(bid % a.n_dm);
   bid /= a.n_dm;
   const int tile = (int)(bid % a.n_tiles);
@@ -198,6 +227,11 @@ __global__ void __launch_bounds__(32 * N1, 16 / N1) search_kernel(const SearchAr
     const int32_t* sh = a.shifts + (size_t)d * a.n_f;
     const int t = t0 + lane;
     const bool tin = t < nv;
+    float2 wf[FOLD];  // W_P^{f r} = W_M^{N f r}
+    static_for<0, FOLD>([&](auto ff) {
+      constexpr int F = decltype(ff)::value;
+      wf[F] = F == 0 ? make_float2(1.f, 0.f) : __ldg(a.tw_m + (N * F * r) % a.M);
+    });
     static_for<0, KPW>([&](auto jj) {
       constexpr int J = decltype(jj)::value;
       const int k0 = warp * KPW + J;
@@ -206,7 +240,17 @@ __global__ void __launch_bounds__(32 * N1, 16 / N1) search_kernel(const SearchAr
         constexpr int K1 = decltype(kk1)::value;
         const int k = k0 + 32 * K1;
         float2 v = make_float2(0.f, 0.f);
-        if (tin) v = __ldg(xb + (size_t)k * a.n_ap + t + __ldg(sh + k));
+        static_for<0, FOLD>([&](auto ff) {
+          constexpr int F = decltype(ff)::value;
+          const int kf = k + N * F;
+          float2 u = make_float2(0.f, 0.f);
+          if (tin) u = __ldg(xb + (size_t)kf * a.n_ap + t + __ldg(sh + kf));
+          if constexpr (F == 0) {
+            v = u;
+          } else {
+            v = cadd(v, cmul(u, wf[F]));
+          }
+        });
         if (r != 0) v = cmul(v, __ldg(a.tw_m + (k * r) % a.M));
         x[K1] = v;
       });
@@ -214,7 +258,8 @@ __global__ void __launch_bounds__(32 * N1, 16 / N1) search_kernel(const SearchAr
       static_for<0, N1>([&](auto mm1) {
         constexpr int M1 = decltype(mm1)::value;
         float2 v = x[bitrev(M1, ilog2(N1))];
-        if constexpr (M1 != 0) v = cmul(v, __ldg(a.tw_n + (k0 * M1) % N));
+        // W_N^{k0 m1} = W_{n_f}^{k0 m1 FOLD}
+        if constexpr (M1 != 0) v = cmul(v, __ldg(a.tw_n + (k0 * M1 * FOLD) % a.n_f));
         S[lane * LD + k0 * N1 + M1] = v;
       });
     });
@@ -237,7 +282,7 @@ __global__ void __launch_bounds__(32 * N1, 16 / N1) search_kernel(const SearchAr
   __syncthreads();
   // ---- stage 3 ----
   const int c = threadIdx.x;
-  const uint32_t m = (uint32_t)(c * a.pad_delay + r);
+  const uint32_t m = (uint32_t)(c * P + r);
   const uint32_t M = (uint32_t)a.M;
   // slot base of window 2^l: segments of the searched smaller windows first
   auto slot_base = [&](int l) {
@@ -284,19 +329,19 @@ __global__ void __launch_bounds__(32 * N1, 16 / N1) search_kernel(const SearchAr
   }
 }
 
-template <int N1, int PADR>
+template <int N1, int PADR, int FOLD>
 static cudaError_t launch_search_t(const SearchArgs& a, cudaStream_t s, int* n_launch) {
   constexpr int N = 32 * N1;
   const size_t smem = (size_t)32 * (N + 1) * sizeof(float2) + (size_t)kMaxSegPerTile * N1 * sizeof(uint2);
-  cudaError_t e = cudaFuncSetAttribute(search_kernel<N1, PADR>,
+  cudaError_t e = cudaFuncSetAttribute(search_kernel<N1, PADR, FOLD>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const long long per_b = (long long)a.n_tiles * a.n_dm * a.pad_delay;
+  const long long per_b = (long long)a.n_tiles * a.n_dm * a.pad_delay * FOLD;
   const long long max_grid = 2147483647LL;
   const int b_chunk = (int)std::max(1LL, std::min((long long)a.n_bl, max_grid / std::max(1LL, per_b)));
   for (int b0 = 0; b0 < a.n_bl; b0 += b_chunk) {
     const int nb = std::min(b_chunk, a.n_bl - b0);
-    search_kernel<N1, PADR><<<(unsigned)(per_b * nb), N, smem, s>>>(a, b0);
+    search_kernel<N1, PADR, FOLD><<<(unsigned)(per_b * nb), N, smem, s>>>(a, b0);
     ++*n_launch;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -304,13 +349,21 @@ static cudaError_t launch_search_t(const SearchArgs& a, cudaStream_t s, int* n_l
   return cudaSuccess;
 }
 
+// Work split of the delay transform by band size: N = n_f / FOLD points
+// per residue FFT, one thread per point.  n_f = 512 runs as one 512-thread
+// CTA per SM (a.fold = 1); a.fold = 2 selects two folded 256-thread CTAs
+// (each gathers twice the input per thread; slower on B300).
 template <int PADR>
 static cudaError_t launch_search_p(const SearchArgs& a, cudaStream_t s, int* n_launch) {
   switch (a.n_f) {
-    case 64: return launch_search_t<2, PADR>(a, s, n_launch);
-    case 128: return launch_search_t<4, PADR>(a, s, n_launch);
-    case 256: return launch_search_t<8, PADR>(a, s, n_launch);
-    case 512: return launch_search_t<16, PADR>(a, s, n_launch);
+    case 64: return launch_search_t<2, PADR, 1>(a, s, n_launch);
+    case 128: return launch_search_t<4, PADR, 1>(a, s, n_launch);
+    case 256: return launch_search_t<8, PADR, 1>(a, s, n_launch);
+    case 512:
+      return a.fold == 2 ? launch_search_t<8, PADR, 2>(a, s, n_launch)
+                         : launch_search_t<16, PADR, 1>(a, s, n_launch);
+    case 1024: return launch_search_t<8, PADR, 4>(a, s, n_launch);
+    case 2048: return launch_search_t<8, PADR, 8>(a, s, n_launch);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -94,7 +94,7 @@ def _seg(**kw):
 
 @pytest.mark.parametrize("seg_kw,prm_kw", [
     (dict(n_chan=15), {}),                       # n_f = 60 not a power of two
-    (dict(n_if=32, n_chan=32), {}),              # n_f = 1024 not in this build
+    (dict(n_if=64, n_chan=64), {}),              # n_f = 4096 not in this build
     (dict(n_ap=-1), {}),
     (dict(t_ap_s=0.0), {}),
     (dict(chan_bw_mhz=-0.5), {}),

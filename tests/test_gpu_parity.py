@@ -146,6 +146,10 @@ CONFIGS = [
          windows=(2, 4, 8, 16)),
     dict(name="nf512_w1-32", n_bl=1, n_ap=161, n_if=8, n_chan=64, n_dm=4, dm_step=30.0,
          windows=(1, 2, 4, 8, 16, 32)),
+    dict(name="nf1024_w1-32", n_bl=1, n_ap=140, n_if=8, n_chan=128, n_dm=3, dm_step=40.0,
+         windows=(1, 2, 4, 8, 16, 32)),
+    dict(name="nf2048_w2-32", n_bl=1, n_ap=100, n_if=16, n_chan=128, n_dm=2, dm_step=40.0,
+         windows=(2, 8, 32)),
 ]
 
 
@@ -167,6 +171,20 @@ def test_peaks_stats_candidates_match_oracle(cfg):
     n, ties = check_peaks(wl, g, ref, vis, cal)
     assert n == sum(len(p.P) for p in ref.peaks.values())
     check_candidates(wl, g, ref, matched=True)
+    g.close()
+
+
+def test_512_point_band_folded_matches_oracle(monkeypatch):
+    """n_f = 512 with the folded work split (two 256-thread CTAs of 8
+    residues) instead of the default single 512-thread CTA."""
+    monkeypatch.setenv("VOLKS_SEARCH_FOLD", "2")
+    wl = synth.small(n_bl=1, n_ap=200, n_if=8, n_chan=64, n_dm=3, dm_step=30.0,
+                     windows=(1, 2, 4, 8, 16, 32), min_baselines=1)
+    vis, cal, _ = make_data(wl, seed=21)
+    g = gpu_search(wl, vis, cal)
+    ref = O.search(wl, vis, cal)
+    check_peaks(wl, g, ref, vis, cal)
+    check_candidates(wl, g, ref)
     g.close()
 
 
