@@ -175,6 +175,19 @@ int volks_shift_table(double f_lo_mhz, double chan_bw_mhz, int32_t n_f, double t
                       int32_t n_ap, double dm_lo, double dm_step, int32_t n_dm,
                       int32_t *shifts, int32_t *nvalid);
 
+/*
+ * Host only, no device work: the cross-baseline match of step a10 (Sec.
+ * 3.1.1 item 3) over window-matched candidates gathered from several
+ * searches of one scan (e.g. baselines split over GPUs, each searched with
+ * min_baselines = 1).  Entries at one dm_idx whose [t0_ap, t1_ap) overlap
+ * form one pulse; pulses on >= min_baselines distinct `bl` values are kept,
+ * with n_baselines set, sorted by (dm_idx, t0_ap, bl).  `in` (n entries)
+ * and `out` (cap entries) are host arrays; *n_out receives the full count.
+ * volks_candidates applies the same rule to one search's own list.
+ */
+int volks_cross_match(const volks_candidate *in, size_t n, int32_t min_baselines,
+                      volks_candidate *out, size_t cap, size_t *n_out);
+
 /* ---- introspection, for checking each step against a reference ---- */
 
 /* Waits for the search.  Stage times and launch counts. */

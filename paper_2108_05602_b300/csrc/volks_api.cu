@@ -179,6 +179,43 @@ int shift_table(double f_lo_mhz, double chan_bw_mhz, int n_f, double t_ap_s, int
   return 0;
 }
 
+// a10 (Sec. 3.1.1 item 3): at one DM, entries of different baselines whose
+// representative intervals [t0_ap, t1_ap) overlap are one pulse; keep the
+// pulses seen on >= min_baselines distinct baselines, each entry carrying
+// n_baselines; output sorted by (dm_idx, t0_ap, bl).
+std::vector<volks_candidate> cross_match(std::vector<volks_candidate> all, int min_baselines) {
+  std::sort(all.begin(), all.end(), [](const volks_candidate& a, const volks_candidate& b) {
+    if (a.dm_idx != b.dm_idx) return a.dm_idx < b.dm_idx;
+    if (a.t0_ap != b.t0_ap) return a.t0_ap < b.t0_ap;
+    if (a.t1_ap != b.t1_ap) return a.t1_ap < b.t1_ap;
+    return a.bl < b.bl;
+  });
+  std::vector<volks_candidate> out;
+  size_t i = 0;
+  while (i < all.size()) {
+    size_t j = i + 1;
+    int end = all[i].t1_ap;
+    while (j < all.size() && all[j].dm_idx == all[i].dm_idx && all[j].t0_ap < end) {
+      end = std::max(end, all[j].t1_ap);
+      ++j;
+    }
+    std::set<int> bls;
+    for (size_t k = i; k < j; ++k) bls.insert(all[k].bl);
+    if ((int)bls.size() >= min_baselines)
+      for (size_t k = i; k < j; ++k) {
+        all[k].n_baselines = (int)bls.size();
+        out.push_back(all[k]);
+      }
+    i = j;
+  }
+  std::stable_sort(out.begin(), out.end(), [](const volks_candidate& a, const volks_candidate& b) {
+    if (a.dm_idx != b.dm_idx) return a.dm_idx < b.dm_idx;
+    if (a.t0_ap != b.t0_ap) return a.t0_ap < b.t0_ap;
+    return a.bl < b.bl;
+  });
+  return out;
+}
+
 int launch_match_into(volks_result* r) {
   r->match_args.out = r->d_cand;
   r->match_args.cap = r->cap;
@@ -487,35 +524,7 @@ int volks_candidates(volks_result* r, volks_candidate* buf, size_t cap, size_t* 
       o.rate_hz = o.rate_idx / (R * s.t_ap_s);
     }
     // a10: cross-baseline match per DM over representative intervals
-    std::sort(all.begin(), all.end(), [](const volks_candidate& a, const volks_candidate& b) {
-      if (a.dm_idx != b.dm_idx) return a.dm_idx < b.dm_idx;
-      if (a.t0_ap != b.t0_ap) return a.t0_ap < b.t0_ap;
-      if (a.t1_ap != b.t1_ap) return a.t1_ap < b.t1_ap;
-      return a.bl < b.bl;
-    });
-    r->cands.clear();
-    size_t i = 0;
-    while (i < all.size()) {
-      size_t j = i + 1;
-      int end = all[i].t1_ap;
-      while (j < all.size() && all[j].dm_idx == all[i].dm_idx && all[j].t0_ap < end) {
-        end = std::max(end, all[j].t1_ap);
-        ++j;
-      }
-      std::set<int> bls;
-      for (size_t k = i; k < j; ++k) bls.insert(all[k].bl);
-      if ((int)bls.size() >= p.min_baselines)
-        for (size_t k = i; k < j; ++k) {
-          all[k].n_baselines = (int)bls.size();
-          r->cands.push_back(all[k]);
-        }
-      i = j;
-    }
-    std::stable_sort(r->cands.begin(), r->cands.end(), [](const volks_candidate& a, const volks_candidate& b) {
-      if (a.dm_idx != b.dm_idx) return a.dm_idx < b.dm_idx;
-      if (a.t0_ap != b.t0_ap) return a.t0_ap < b.t0_ap;
-      return a.bl < b.bl;
-    });
+    r->cands = cross_match(all, p.min_baselines);
     r->have_cands = true;
   }
   *n_total = r->cands.size();
@@ -525,6 +534,18 @@ int volks_candidates(volks_result* r, volks_candidate* buf, size_t cap, size_t* 
 }
 
 void volks_free(volks_result* r) { release(r); }
+
+int volks_cross_match(const volks_candidate* in, size_t n, int32_t min_baselines, volks_candidate* out,
+                      size_t cap, size_t* n_out) {
+  if (!n_out || (n > 0 && !in) || (cap > 0 && !out)) return fail(VOLKS_EINVAL, "NULL argument");
+  if (min_baselines < 1) return fail(VOLKS_EINVAL, "min_baselines must be >= 1");
+  std::vector<volks_candidate> v(in, in + n);
+  v = cross_match(std::move(v), min_baselines);
+  *n_out = v.size();
+  const size_t k = std::min(cap, v.size());
+  if (k) std::memcpy(out, v.data(), k * sizeof(volks_candidate));
+  return 0;
+}
 
 int volks_shift_table(double f_lo_mhz, double chan_bw_mhz, int32_t n_f, double t_ap_s, int32_t n_ap,
                       double dm_lo, double dm_step, int32_t n_dm, int32_t* shifts, int32_t* nvalid) {

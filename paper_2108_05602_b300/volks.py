@@ -94,6 +94,9 @@ def lib() -> C.CDLL:
     L.volks_result_stats.restype = C.c_int
     L.volks_result_gains.argtypes = [P, C.POINTER(C.c_float), SZ]
     L.volks_result_gains.restype = C.c_int
+    L.volks_cross_match.argtypes = [C.POINTER(volks_candidate), SZ, I32,
+                                    C.POINTER(volks_candidate), SZ, C.POINTER(SZ)]
+    L.volks_cross_match.restype = C.c_int
     L.volks_search_peaks_noalloc.argtypes = [C.POINTER(volks_segment), C.POINTER(volks_params),
                                              P, P, P]
     L.volks_search_peaks_noalloc.restype = C.c_int
@@ -148,6 +151,22 @@ def volks_search_peaks_noalloc(seg: volks_segment, prm: volks_params, stream: in
                                             C.c_void_p(peak_power_ptr),
                                             C.c_void_p(peak_cell_ptr)),
            "volks_search_peaks_noalloc")
+
+
+def volks_cross_match(cands: Sequence[dict], min_baselines: int) -> List[dict]:
+    """Cross-baseline match (a10) of candidate dicts gathered from several
+    searches of one scan; returns the kept entries as dicts."""
+    n = len(cands)
+    arr = (volks_candidate * max(1, n))()
+    names = [k for k, _ in volks_candidate._fields_ if k != "_pad"]
+    for i, c in enumerate(cands):
+        for k in names:
+            setattr(arr[i], k, c[k])
+    out = (volks_candidate * max(1, n))()
+    n_out = C.c_size_t()
+    _check(lib().volks_cross_match(arr, n, min_baselines, out, n, C.byref(n_out)),
+           "volks_cross_match")
+    return [out[i].as_dict() for i in range(n_out.value)]
 
 
 def volks_shift_table(f_lo_mhz, chan_bw_mhz, n_f, t_ap_s, n_ap, dm_lo, dm_step, n_dm):
