@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libvolks.so")
 SOURCES = ["volks_kernels.cu", "volks_api.cu", "volks_noalloc.cu"]
-HEADERS = ["fft_regs.cuh", "twiddle_ce.h", "volks_internal.h",
+HEADERS = ["fft_regs.cuh", "twiddle_ce.h", "volks_internal.h", "volks_job.h", "volks_result.h",
            os.path.join("..", "..", "include", "volks.h")]
 
 

@@ -1,12 +1,13 @@
-// Host side of the C ABI declared in include/volks.h: validation, the FP64
-// shift table, stream-ordered scratch, kernel launches, the cross-baseline
-// match (a10) and result accessors.
+// Host side of the single-segment C ABI declared in include/volks.h:
+// validation, the FP64 shift table, stream-ordered scratch, kernel
+// launches, the cross-baseline match (a10) and result accessors.
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <set>
 #include <string>
 #include <vector>
@@ -15,10 +16,37 @@
 
 #include "../../include/volks.h"
 #include "volks_internal.h"
+#include "volks_job.h"
+#include "volks_result.h"
 
 namespace {
 
 thread_local std::string g_err;
+
+// Cold-plasma dispersion constant, s MHz^2 pc^-1 cm^3.
+constexpr double kDispersion = 4.148808e3;
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+bool is_pow2(long long x) { return x > 0 && (x & (x - 1)) == 0; }
+int ilog2i(int x) {
+  int l = 0;
+  while ((1 << l) < x) ++l;
+  return l;
+}
+
+template <class T>
+cudaError_t dalloc(T** p, size_t n, cudaStream_t s, bool ordered) {
+  *p = nullptr;
+  if (n == 0) return cudaSuccess;
+  return ordered ? cudaMallocAsync(reinterpret_cast<void**>(p), n * sizeof(T), s)
+                 : cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T));
+}
+
+}  // namespace
+
+namespace vk {
+
+void set_last_error(const char* msg) { g_err = msg; }
 
 int fail(int code, const char* fmt, ...) {
   char buf[512];
@@ -35,78 +63,18 @@ int cuda_fail(cudaError_t e, const char* what) {
   return fail(code, "%s: %s", what, cudaGetErrorString(e));
 }
 
-// Cold-plasma dispersion constant, s MHz^2 pc^-1 cm^3.
-constexpr double kDispersion = 4.148808e3;
-constexpr double kTwoPi = 6.283185307179586476925286766559;
-
-bool is_pow2(long long x) { return x > 0 && (x & (x - 1)) == 0; }
-int ilog2i(int x) {
-  int l = 0;
-  while ((1 << l) < x) ++l;
-  return l;
-}
-
-}  // namespace
-
-void vk::set_last_error(const char* msg) { g_err = msg; }
-
-struct volks_result {
-  cudaStream_t stream = nullptr;
-  volks_segment seg{};
-  volks_params prm{};
-  int n_f = 0, M = 0, n_eff = 0, n_tiles = 0;
-  int win_log[vk::kMaxWinLog + 1] = {};
-  int win_off[vk::kMaxWinLog + 1] = {};   // segment offset, by window index
-  int word_off[vk::kMaxWinLog + 1] = {};  // bit-word offset, by window index
-  long long seg_per_bd = 0, word_per_bd = 0;
-  std::vector<int32_t> shifts, nvalid;
-  const float2* d_vis = nullptr;          // caller's device buffer or our copy
-  void* d_vis_copy = nullptr;
-  float2* d_xn = nullptr;
-  double* d_part = nullptr;
-  double2* d_phasor = nullptr;
-  float2* d_gain = nullptr;
-  int32_t* d_shifts = nullptr;
-  int32_t* d_nvalid = nullptr;
-  float2* d_tw_n = nullptr;
-  float2* d_tw_m = nullptr;
-  unsigned long long* d_keys = nullptr;
-  double* d_stats = nullptr;
-  uint32_t* d_bits = nullptr;
-  vk::DevCand* d_cand = nullptr;
-  unsigned int* d_count = nullptr;
-  unsigned int cap = 0;
-  cudaEvent_t ev[6] = {};
-  int n_launch = 0, n_search_launch = 0;
-  bool empty = true, synced = false, have_cands = false;
-  std::vector<volks_candidate> cands;
-  // host staging that must outlive the asynchronous copies
-  std::vector<double2> h_phasor;
-  std::vector<float2> h_tw_n, h_tw_m;
-  vk::MatchArgs match_args{};
-};
-
-namespace {
-
-template <class T>
-cudaError_t dalloc(T** p, size_t n, cudaStream_t s) {
-  *p = nullptr;
-  if (n == 0) return cudaSuccess;
-  return cudaMallocAsync(reinterpret_cast<void**>(p), n * sizeof(T), s);
-}
-
-void release(volks_result* r) {
-  if (!r) return;
-  void* ptrs[] = {r->d_vis_copy, r->d_xn, r->d_part, r->d_phasor, r->d_gain, r->d_shifts,
-                  r->d_nvalid, r->d_tw_n, r->d_tw_m, r->d_keys, r->d_stats, r->d_bits,
-                  r->d_cand, r->d_count};
-  for (void* p : ptrs)
-    if (p) cudaFreeAsync(p, r->stream);
-  // the host staging vectors may still feed in-flight copies
-  if (!r->synced) cudaStreamSynchronize(r->stream);
-  for (auto& e : r->ev)
-    if (e) cudaEventDestroy(e);
-  delete r;
+int sm_count() {
+  static std::mutex mu;
+  static int cache[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!cache[dev]) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+    cache[dev] = n;
+  }
+  return cache[dev];
 }
 
 int validate(const volks_segment* s, const volks_params* p) {
@@ -127,7 +95,8 @@ int validate(const volks_segment* s, const volks_params* p) {
     return fail(VOLKS_EINVAL, "negative DM trial");
   if (p->n_win < 1 || p->n_win > VOLKS_MAX_WIN) return fail(VOLKS_EINVAL, "n_win must be 1..%d", VOLKS_MAX_WIN);
   for (int i = 0; i < p->n_win; ++i) {
-    if (!is_pow2(p->win[i]) || p->win[i] > 32) return fail(VOLKS_EINVAL, "win[%d] = %d: powers of two 1..32 only", i, p->win[i]);
+    if (!is_pow2(p->win[i]) || p->win[i] > 32)
+      return fail(VOLKS_EINVAL, "win[%d] = %d: powers of two 1..32 only", i, p->win[i]);
     if (i > 0 && p->win[i] <= p->win[i - 1]) return fail(VOLKS_EINVAL, "windows must be strictly ascending");
   }
   if (!(p->pad_delay == 1 || p->pad_delay == 2 || p->pad_delay == 4 || p->pad_delay == 8))
@@ -135,30 +104,12 @@ int validate(const volks_segment* s, const volks_params* p) {
   if (!(p->pad_rate == 0 || p->pad_rate == 4)) return fail(VOLKS_EINVAL, "pad_rate must be 0 or 4");
   if (p->precision != VOLKS_FP32) return fail(VOLKS_EINVAL, "precision %d not available", p->precision);
   if (!std::isfinite(p->thresh)) return fail(VOLKS_EINVAL, "thresh not finite");
-  if (p->min_windows < 1 || p->min_baselines < 1) return fail(VOLKS_EINVAL, "min_windows and min_baselines must be >= 1");
+  if (p->min_windows < 1 || p->min_baselines < 1)
+    return fail(VOLKS_EINVAL, "min_windows and min_baselines must be >= 1");
   if ((p->normalize_chan & ~1) || (p->skip_first_chan & ~1)) return fail(VOLKS_EINVAL, "flags must be 0 or 1");
   return 0;
 }
 
-int sync_result(volks_result* r) {
-  if (r->synced) return 0;
-  cudaError_t e = cudaStreamSynchronize(r->stream);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
-  r->synced = true;
-  return 0;
-}
-
-#define VK_TRY(expr, what)                              \
-  do {                                                  \
-    cudaError_t e_ = (expr);                            \
-    if (e_ != cudaSuccess) {                            \
-      int rc_ = cuda_fail(e_, what);                    \
-      release(r);                                       \
-      return rc_;                                       \
-    }                                                   \
-  } while (0)
-
-// a1 (see volks_shift_table in volks.h).
 int shift_table(double f_lo_mhz, double chan_bw_mhz, int n_f, double t_ap_s, int n_ap, double dm_lo,
                 double dm_step, int n_dm, int32_t* shifts, int32_t* nvalid) {
   std::vector<double> f(n_f);
@@ -179,10 +130,6 @@ int shift_table(double f_lo_mhz, double chan_bw_mhz, int n_f, double t_ap_s, int
   return 0;
 }
 
-// a10 (Sec. 3.1.1 item 3): at one DM, entries of different baselines whose
-// representative intervals [t0_ap, t1_ap) overlap are one pulse; keep the
-// pulses seen on >= min_baselines distinct baselines, each entry carrying
-// n_baselines; output sorted by (dm_idx, t0_ap, bl).
 std::vector<volks_candidate> cross_match(std::vector<volks_candidate> all, int min_baselines) {
   std::sort(all.begin(), all.end(), [](const volks_candidate& a, const volks_candidate& b) {
     if (a.dm_idx != b.dm_idx) return a.dm_idx < b.dm_idx;
@@ -216,17 +163,268 @@ std::vector<volks_candidate> cross_match(std::vector<volks_candidate> all, int m
   return out;
 }
 
-int launch_match_into(volks_result* r) {
-  r->match_args.out = r->d_cand;
-  r->match_args.cap = r->cap;
-  cudaError_t e = cudaMemsetAsync(r->d_count, 0, sizeof(unsigned int), r->stream);
-  if (e != cudaSuccess) return cuda_fail(e, "memset count");
-  e = vk::launch_match(r->match_args, r->stream, &r->n_launch);
-  if (e != cudaSuccess) return cuda_fail(e, "match kernel");
+// ------------------------------------------------------------- SegJob ----
+int SegJob::init(const volks_segment& s, const volks_params& p, int chunk) {
+  seg = s;
+  prm = p;
+  n_f = s.n_if * s.n_chan;
+  M = p.pad_delay * n_f;
+  n_eff = n_f - (p.skip_first_chan ? s.n_if : 0);
+  n_tiles = (s.n_ap + kTile - 1) / kTile;
+  n_tchunk = (s.n_ap + tchunk - 1) / tchunk;
+  win_mask = 0;
+  long long so = 0, wo = 0;
+  for (int l = 0; l <= kMaxWinLog; ++l) win_off_l[l] = 0;
+  for (int i = 0; i < p.n_win; ++i) {
+    win_log[i] = ilog2i(p.win[i]);
+    win_off[i] = (int)so;
+    word_off[i] = (int)wo;
+    win_off_l[win_log[i]] = (int)so;
+    const long long ns = s.n_ap / p.win[i];
+    so += ns;
+    wo += (ns + 31) / 32;
+    win_mask |= 1 << win_log[i];
+  }
+  seg_per_bd = so;
+  word_per_bd = wo;
+  dm_chunk = (chunk <= 0 || chunk > p.n_dm) ? std::max(1, p.n_dm) : chunk;
+  empty = ((long long)s.n_bl * s.n_ap * p.n_dm == 0);
+  shifts.assign((size_t)p.n_dm * n_f, 0);
+  nvalid.assign(p.n_dm, 0);
+  int rc = shift_table(s.f_lo_mhz, s.chan_bw_mhz, n_f, s.t_ap_s, s.n_ap, p.dm_lo, p.dm_step, p.n_dm,
+                       shifts.data(), nvalid.data());
+  if (rc) return rc;
+  h_phasor.resize((size_t)s.n_bl * n_f);
+  for (int b = 0; b < s.n_bl; ++b)
+    for (int k = 0; k < n_f; ++k) {
+      const int n = k / s.n_chan, j = k % s.n_chan;
+      double ph = 0.0;
+      if (s.cal) {
+        const double fj = (j + 0.5) * s.chan_bw_mhz * 1e6;
+        ph = kTwoPi * fj * s.cal[((size_t)b * s.n_if + n) * 2 + 0] + s.cal[((size_t)b * s.n_if + n) * 2 + 1];
+      }
+      h_phasor[(size_t)b * n_f + k] = make_double2(std::cos(ph), -std::sin(ph));
+    }
+  seg.cal = nullptr;  // the calibration table is read during the creating call only
+  h_tw_n.resize(n_f);
+  for (int i = 0; i < n_f; ++i)
+    h_tw_n[i] = make_float2((float)std::cos(kTwoPi * i / n_f), (float)-std::sin(kTwoPi * i / n_f));
+  h_tw_m.resize(M);
+  for (int i = 0; i < M; ++i)
+    h_tw_m[i] = make_float2((float)std::cos(kTwoPi * i / M), (float)-std::sin(kTwoPi * i / M));
+  cap = (unsigned)std::max<long long>(4096, std::min<long long>(1LL << 24, (long long)s.n_bl * p.n_dm * 64));
   return 0;
 }
 
+size_t SegJob::device_bytes() const {
+  const size_t vis_n = (size_t)seg.n_bl * seg.n_ap * n_f;
+  return vis_n * 8 + (size_t)seg.n_bl * n_tchunk * n_f * 8 + (size_t)seg.n_bl * n_f * 24 +
+         (size_t)prm.n_dm * (n_f + 1) * 4 + (size_t)(n_f + M) * 8 + keys_bytes_per_dm() * dm_chunk +
+         (size_t)seg.n_bl * prm.n_dm * prm.n_win * 16 + (size_t)seg.n_bl * dm_chunk * word_per_bd * 4 +
+         (size_t)cap * sizeof(DevCand) + 4;
+}
+
+int SegJob::alloc(cudaStream_t s, bool ordered) {
+  stream_ordered = ordered;
+  cudaError_t e;
+#define VK_A(ptr, n, what)                                 \
+  if ((e = dalloc(&ptr, (n), s, ordered)) != cudaSuccess) \
+    return cuda_fail(e, what);
+  VK_A(d_cand, cap, "alloc candidates");
+  VK_A(d_count, 1, "alloc count");
+  if (empty) return 0;
+  const size_t vis_n = (size_t)seg.n_bl * seg.n_ap * n_f;
+  VK_A(d_xn, vis_n, "alloc normalised copy");
+  VK_A(d_part, (size_t)seg.n_bl * n_tchunk * n_f, "alloc partial sums");
+  VK_A(d_phasor, (size_t)seg.n_bl * n_f, "alloc phasor");
+  VK_A(d_gain, (size_t)seg.n_bl * n_f, "alloc gains");
+  VK_A(d_shifts, (size_t)prm.n_dm * n_f, "alloc shifts");
+  VK_A(d_nvalid, (size_t)prm.n_dm, "alloc nvalid");
+  VK_A(d_tw_n, (size_t)n_f, "alloc twiddles");
+  VK_A(d_tw_m, (size_t)M, "alloc twiddles");
+  VK_A(d_keys, (size_t)seg.n_bl * dm_chunk * seg_per_bd, "alloc peaks");
+  VK_A(d_stats, (size_t)seg.n_bl * prm.n_dm * prm.n_win * 2, "alloc stats");
+  VK_A(d_bits, (size_t)seg.n_bl * dm_chunk * word_per_bd, "alloc bitmaps");
+#undef VK_A
+  return 0;
+}
+
+int SegJob::stage_input(cudaStream_t s) {
+  if (empty) return 0;
+  const size_t vis_n = (size_t)seg.n_bl * seg.n_ap * n_f;
+  cudaPointerAttributes attr{};
+  if (cudaPointerGetAttributes(&attr, seg.vis) != cudaSuccess) {
+    cudaGetLastError();
+    attr.type = cudaMemoryTypeUnregistered;
+  }
+  if (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged) {
+    d_vis = static_cast<const float2*>(seg.vis);
+    return 0;
+  }
+  cudaError_t e = stream_ordered ? cudaMallocAsync(&d_vis_copy, vis_n * sizeof(float2), s)
+                                 : cudaMalloc(&d_vis_copy, vis_n * sizeof(float2));
+  if (e != cudaSuccess) return cuda_fail(e, "alloc vis copy");
+  e = cudaMemcpyAsync(d_vis_copy, seg.vis, vis_n * sizeof(float2), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(e, "copy vis to device");
+  d_vis = static_cast<const float2*>(d_vis_copy);
+  return 0;
+}
+
+int SegJob::upload(cudaStream_t s) {
+  if (empty) return 0;
+  cudaError_t e;
+#define VK_C(dst, src, what)                                                                  \
+  if ((e = cudaMemcpyAsync(dst, (src).data(), (src).size() * sizeof((src)[0]),                \
+                           cudaMemcpyHostToDevice, s)) != cudaSuccess)                        \
+    return cuda_fail(e, what);
+  VK_C(d_phasor, h_phasor, "copy phasor");
+  VK_C(d_shifts, shifts, "copy shifts");
+  VK_C(d_nvalid, nvalid, "copy nvalid");
+  VK_C(d_tw_n, h_tw_n, "copy twiddles");
+  VK_C(d_tw_m, h_tw_m, "copy twiddles");
+#undef VK_C
+  return 0;
+}
+
+void SegJob::release(cudaStream_t s) {
+  void* ptrs[] = {d_vis_copy, d_xn,   d_part,  d_phasor, d_gain, d_shifts, d_nvalid,
+                  d_tw_n,     d_tw_m, d_keys,  d_stats,  d_bits, d_cand,   d_count};
+  for (void* p : ptrs)
+    if (p) {
+      if (stream_ordered) cudaFreeAsync(p, s);
+      else cudaFree(p);
+    }
+  d_vis_copy = nullptr;
+  d_xn = nullptr;
+  d_part = nullptr;
+  d_phasor = nullptr;
+  d_gain = nullptr;
+  d_shifts = nullptr;
+  d_nvalid = nullptr;
+  d_tw_n = d_tw_m = nullptr;
+  d_keys = nullptr;
+  d_stats = nullptr;
+  d_bits = nullptr;
+  d_cand = nullptr;
+  d_count = nullptr;
+}
+
+SegDesc SegJob::desc(int c) const {
+  SegDesc d;
+  std::memset(&d, 0, sizeof d);
+  const int d0 = c * dm_chunk;
+  d.xn = d_xn;
+  d.shifts = d_shifts + (size_t)d0 * n_f;
+  d.nvalid = d_nvalid + d0;
+  d.tw_n = d_tw_n;
+  d.tw_m = d_tw_m;
+  d.keys = d_keys;
+  d.stats = d_stats;
+  d.bits = d_bits;
+  d.cand = d_cand;
+  d.count = d_count;
+  d.cap = cap;
+  d.seg_id = seg_id;
+  d.seg_per_bd = seg_per_bd;
+  d.word_per_bd = word_per_bd;
+  d.n_bl = seg.n_bl;
+  d.n_ap = seg.n_ap;
+  d.n_f = n_f;
+  d.n_dm = std::min(dm_chunk, prm.n_dm - d0);
+  d.n_dm_total = prm.n_dm;
+  d.d0 = d0;
+  d.pad_delay = prm.pad_delay;
+  d.M = M;
+  d.n_tiles = n_tiles;
+  d.n_win = prm.n_win;
+  d.n_eff = n_eff;
+  d.min_windows = prm.min_windows;
+  d.win_mask = win_mask;
+  for (int i = 0; i <= kMaxWinLog; ++i) {
+    d.win_log[i] = win_log[i];
+    d.win_off[i] = win_off[i];
+    d.word_off[i] = word_off[i];
+    d.win_off_l[i] = win_off_l[i];
+  }
+  d.thresh = prm.thresh;
+  return d;
+}
+
+cudaError_t SegJob::enqueue_prep(cudaStream_t s, int* n_launch) const {
+  PrepArgs pa{};
+  pa.vis = d_vis;
+  pa.xn = d_xn;
+  pa.part = d_part;
+  pa.phasor = d_phasor;
+  pa.gain = d_gain;
+  pa.n_bl = seg.n_bl;
+  pa.n_ap = seg.n_ap;
+  pa.n_f = n_f;
+  pa.n_chan = seg.n_chan;
+  pa.n_tchunk = n_tchunk;
+  pa.tchunk = tchunk;
+  pa.normalize = prm.normalize_chan;
+  pa.skip_first_chan = prm.skip_first_chan;
+  return launch_prep(pa, s, n_launch);
+}
+
+}  // namespace vk
+
+// ============================================================ results ====
+namespace {
+
+using vk::cuda_fail;
+using vk::fail;
+
+void release(volks_result* r) {
+  if (!r || r->borrowed) return;
+  if (r->own_job) {
+    r->own_job->release(r->stream);
+    // the job's host vectors may still feed in-flight copies
+    if (!r->synced) cudaStreamSynchronize(r->stream);
+    delete r->own_job;
+  }
+  if (r->counter) cudaFreeAsync(r->counter, r->stream);
+  for (auto& e : r->ev)
+    if (e) cudaEventDestroy(e);
+  delete r;
+}
+
+int sync_result(volks_result* r) {
+  if (r->synced) return 0;
+  cudaError_t e = cudaStreamSynchronize(r->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  r->synced = true;
+  return 0;
+}
+
+#define VK_TRY(expr, what)           \
+  do {                               \
+    cudaError_t e_ = (expr);         \
+    if (e_ != cudaSuccess) {         \
+      int rc_ = cuda_fail(e_, what); \
+      release(r);                    \
+      return rc_;                    \
+    }                                \
+  } while (0)
+
 }  // namespace
+
+int vk_rerun_match(volks_result* r) {
+  vk::SegJob* j = r->job;
+  cudaError_t e = cudaMemsetAsync(j->d_count, 0, sizeof(unsigned int), r->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "memset count");
+  vk::Batch b;
+  std::memset(&b, 0, sizeof b);
+  b.d[0] = j->desc(0);
+  b.n_desc = 1;
+  b.total = (long long)j->seg.n_bl * b.d[0].n_dm;
+  int n = 0;
+  e = vk::launch_match_batch(b, r->stream, &n);
+  if (e != cudaSuccess) return cuda_fail(e, "match kernel");
+  r->synced = false;
+  return 0;
+}
 
 extern "C" {
 
@@ -257,212 +455,80 @@ int volks_search_segment(const volks_segment* seg, const volks_params* prm, void
                          volks_result** out) {
   if (!out) return fail(VOLKS_EINVAL, "out is NULL");
   *out = nullptr;
-  int rc = validate(seg, prm);
+  int rc = vk::validate(seg, prm);
   if (rc) return rc;
-
   volks_result* r = new (std::nothrow) volks_result();
   if (!r) return fail(VOLKS_ENOMEM, "host allocation");
-  r->stream = static_cast<cudaStream_t>(cuda_stream);
-  r->seg = *seg;
-  r->prm = *prm;
-  const int n_bl = seg->n_bl, n_ap = seg->n_ap, n_f = seg->n_if * seg->n_chan;
-  const int n_dm = prm->n_dm, n_win = prm->n_win;
-  r->n_f = n_f;
-  r->M = prm->pad_delay * n_f;
-  r->n_eff = n_f - (prm->skip_first_chan ? seg->n_if : 0);
-  r->n_tiles = (n_ap + vk::kTile - 1) / vk::kTile;
-  int win_mask = 0;
-  long long so = 0, wo = 0;
-  for (int i = 0; i < n_win; ++i) {
-    r->win_log[i] = ilog2i(prm->win[i]);
-    r->win_off[i] = (int)so;
-    r->word_off[i] = (int)wo;
-    const long long ns = n_ap / prm->win[i];
-    so += ns;
-    wo += (ns + 31) / 32;
-    win_mask |= 1 << r->win_log[i];
+  r->own_job = new (std::nothrow) vk::SegJob();
+  if (!r->own_job) {
+    delete r;
+    return fail(VOLKS_ENOMEM, "host allocation");
   }
-  r->seg_per_bd = so;
-  r->word_per_bd = wo;
-
-  // a1: shift table, FP64 on the host, rounded half-up (Sec. 2.4.2 step 4).
-  r->shifts.resize((size_t)n_dm * n_f);
-  r->nvalid.resize(n_dm);
-  rc = shift_table(seg->f_lo_mhz, seg->chan_bw_mhz, n_f, seg->t_ap_s, n_ap, prm->dm_lo, prm->dm_step,
-                   n_dm, r->shifts.data(), r->nvalid.data());
+  r->job = r->own_job;
+  r->stream = static_cast<cudaStream_t>(cuda_stream);
+  vk::SegJob& j = *r->job;
+  rc = j.init(*seg, *prm, 0);
   if (rc) {
     release(r);
     return rc;
   }
-  r->empty = ((long long)n_bl * n_ap * n_dm == 0);
-
   for (auto& e : r->ev) VK_TRY(cudaEventCreate(&e), "cudaEventCreate");
   cudaStream_t st = r->stream;
   VK_TRY(cudaEventRecord(r->ev[0], st), "event");
-
-  // candidates buffer exists even for an empty search
-  r->cap = (unsigned)std::max<long long>(4096, std::min<long long>(1LL << 24, (long long)n_bl * n_dm * 64));
-  VK_TRY(dalloc(&r->d_cand, r->cap, st), "alloc candidates");
-  VK_TRY(dalloc(&r->d_count, 1, st), "alloc count");
-  VK_TRY(cudaMemsetAsync(r->d_count, 0, sizeof(unsigned int), st), "memset count");
-
-  if (r->empty) {
+  rc = j.alloc(st, true);
+  if (!rc) rc = j.stage_input(st);
+  if (rc) {
+    release(r);
+    return rc;
+  }
+  VK_TRY(cudaMemsetAsync(j.d_count, 0, sizeof(unsigned int), st), "memset count");
+  if (j.empty) {
     for (int i = 1; i < 6; ++i) VK_TRY(cudaEventRecord(r->ev[i], st), "event");
     *out = r;
     return 0;
   }
-
-  // input: the caller's device buffer, or a stream-ordered copy of host memory
-  const size_t vis_n = (size_t)n_bl * n_ap * n_f;
-  cudaPointerAttributes attr{};
-  cudaError_t pe = cudaPointerGetAttributes(&attr, seg->vis);
-  if (pe != cudaSuccess) {
-    cudaGetLastError();
-    attr.type = cudaMemoryTypeUnregistered;
-  }
-  if (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged) {
-    r->d_vis = static_cast<const float2*>(seg->vis);
-  } else {
-    VK_TRY(cudaMallocAsync(&r->d_vis_copy, vis_n * sizeof(float2), st), "alloc vis copy");
-    VK_TRY(cudaMemcpyAsync(r->d_vis_copy, seg->vis, vis_n * sizeof(float2), cudaMemcpyHostToDevice, st),
-           "copy vis to device");
-    r->d_vis = static_cast<const float2*>(r->d_vis_copy);
-  }
   VK_TRY(cudaEventRecord(r->ev[1], st), "event");
-
-  // calibration phasor (FP64) and FFT twiddles, computed on the host
-  r->h_phasor.resize((size_t)n_bl * n_f);
-  for (int b = 0; b < n_bl; ++b)
-    for (int k = 0; k < n_f; ++k) {
-      const int n = k / seg->n_chan, j = k % seg->n_chan;
-      double ph = 0.0;
-      if (seg->cal) {
-        const double fj = (j + 0.5) * seg->chan_bw_mhz * 1e6;
-        ph = kTwoPi * fj * seg->cal[((size_t)b * seg->n_if + n) * 2 + 0] + seg->cal[((size_t)b * seg->n_if + n) * 2 + 1];
-      }
-      r->h_phasor[(size_t)b * n_f + k] = make_double2(std::cos(ph), -std::sin(ph));
-    }
-  r->h_tw_n.resize(n_f);
-  for (int i = 0; i < n_f; ++i)
-    r->h_tw_n[i] = make_float2((float)std::cos(kTwoPi * i / n_f), (float)-std::sin(kTwoPi * i / n_f));
-  r->h_tw_m.resize(r->M);
-  for (int i = 0; i < r->M; ++i)
-    r->h_tw_m[i] = make_float2((float)std::cos(kTwoPi * i / r->M), (float)-std::sin(kTwoPi * i / r->M));
-
-  const int tchunk = 1024;
-  const int n_tchunk = (n_ap + tchunk - 1) / tchunk;
-  VK_TRY(dalloc(&r->d_xn, vis_n, st), "alloc normalised copy");
-  VK_TRY(dalloc(&r->d_part, (size_t)n_bl * n_tchunk * n_f, st), "alloc partial sums");
-  VK_TRY(dalloc(&r->d_phasor, (size_t)n_bl * n_f, st), "alloc phasor");
-  VK_TRY(dalloc(&r->d_gain, (size_t)n_bl * n_f, st), "alloc gains");
-  VK_TRY(dalloc(&r->d_shifts, (size_t)n_dm * n_f, st), "alloc shifts");
-  VK_TRY(dalloc(&r->d_nvalid, (size_t)n_dm, st), "alloc nvalid");
-  VK_TRY(dalloc(&r->d_tw_n, (size_t)n_f, st), "alloc twiddles");
-  VK_TRY(dalloc(&r->d_tw_m, (size_t)r->M, st), "alloc twiddles");
-  const size_t n_keys = (size_t)n_bl * n_dm * r->seg_per_bd;
-  VK_TRY(dalloc(&r->d_keys, n_keys, st), "alloc peaks");
-  VK_TRY(dalloc(&r->d_stats, (size_t)n_bl * n_dm * n_win * 2, st), "alloc stats");
-  VK_TRY(dalloc(&r->d_bits, (size_t)n_bl * n_dm * r->word_per_bd, st), "alloc bitmaps");
-  VK_TRY(cudaMemcpyAsync(r->d_phasor, r->h_phasor.data(), r->h_phasor.size() * sizeof(double2),
-                         cudaMemcpyHostToDevice, st), "copy phasor");
-  VK_TRY(cudaMemcpyAsync(r->d_shifts, r->shifts.data(), r->shifts.size() * sizeof(int32_t),
-                         cudaMemcpyHostToDevice, st), "copy shifts");
-  VK_TRY(cudaMemcpyAsync(r->d_nvalid, r->nvalid.data(), r->nvalid.size() * sizeof(int32_t),
-                         cudaMemcpyHostToDevice, st), "copy nvalid");
-  VK_TRY(cudaMemcpyAsync(r->d_tw_n, r->h_tw_n.data(), r->h_tw_n.size() * sizeof(float2),
-                         cudaMemcpyHostToDevice, st), "copy twiddles");
-  VK_TRY(cudaMemcpyAsync(r->d_tw_m, r->h_tw_m.data(), r->h_tw_m.size() * sizeof(float2),
-                         cudaMemcpyHostToDevice, st), "copy twiddles");
-  VK_TRY(cudaMemsetAsync(r->d_keys, 0, n_keys * sizeof(unsigned long long), st), "memset peaks");
-
-  // a2-a3
-  vk::PrepArgs pa{};
-  pa.vis = r->d_vis;
-  pa.xn = r->d_xn;
-  pa.part = r->d_part;
-  pa.phasor = r->d_phasor;
-  pa.gain = r->d_gain;
-  pa.n_bl = n_bl;
-  pa.n_ap = n_ap;
-  pa.n_f = n_f;
-  pa.n_chan = seg->n_chan;
-  pa.n_tchunk = n_tchunk;
-  pa.tchunk = tchunk;
-  pa.normalize = prm->normalize_chan;
-  pa.skip_first_chan = prm->skip_first_chan;
-  VK_TRY(vk::launch_prep(pa, st, &r->n_launch), "prep kernels");
-  VK_TRY(cudaEventRecord(r->ev[2], st), "event");
-
-  // a4-a7
-  vk::SearchArgs sa{};
-  sa.xn = r->d_xn;
-  sa.shifts = r->d_shifts;
-  sa.nvalid = r->d_nvalid;
-  sa.tw_n = r->d_tw_n;
-  sa.tw_m = r->d_tw_m;
-  sa.keys = r->d_keys;
-  sa.n_bl = n_bl;
-  sa.n_ap = n_ap;
-  sa.n_f = n_f;
-  sa.n_dm = n_dm;
-  sa.pad_delay = prm->pad_delay;
-  sa.M = r->M;
-  sa.win_mask = win_mask;
-  for (int i = 0; i < n_win; ++i) sa.win_off[r->win_log[i]] = r->win_off[i];
-  sa.seg_per_bd = r->seg_per_bd;
-  sa.n_tiles = r->n_tiles;
-  sa.fold = 1;  // measured: one 512-thread CTA beats two folded 256-thread CTAs at n_f = 512
-  if (const char* f = std::getenv("VOLKS_SEARCH_FOLD")) sa.fold = std::atoi(f);
-  const int before = r->n_launch;
-  VK_TRY(vk::launch_search(sa, prm->pad_rate, st, &r->n_launch), "search kernel");
-  r->n_search_launch = r->n_launch - before;
-  VK_TRY(cudaEventRecord(r->ev[3], st), "event");
-
-  // a8
-  vk::SelectArgs ea{};
-  ea.keys = r->d_keys;
-  ea.nvalid = r->d_nvalid;
-  ea.stats = r->d_stats;
-  ea.bits = r->d_bits;
-  ea.n_bl = n_bl;
-  ea.n_dm = n_dm;
-  ea.n_win = n_win;
-  ea.n_eff = r->n_eff;
-  for (int i = 0; i < n_win; ++i) {
-    ea.win_log[i] = r->win_log[i];
-    ea.win_off[i] = r->win_off[i];
-    ea.word_off[i] = r->word_off[i];
-  }
-  ea.seg_per_bd = r->seg_per_bd;
-  ea.word_per_bd = r->word_per_bd;
-  ea.thresh = prm->thresh;
-  VK_TRY(vk::launch_select(ea, st, &r->n_launch), "select kernel");
-  VK_TRY(cudaEventRecord(r->ev[4], st), "event");
-
-  // a9
-  vk::MatchArgs& ma = r->match_args;
-  ma.keys = r->d_keys;
-  ma.stats = r->d_stats;
-  ma.bits = r->d_bits;
-  ma.nvalid = r->d_nvalid;
-  ma.count = r->d_count;
-  ma.n_bl = n_bl;
-  ma.n_dm = n_dm;
-  ma.n_win = n_win;
-  ma.n_eff = r->n_eff;
-  ma.min_windows = prm->min_windows;
-  for (int i = 0; i < n_win; ++i) {
-    ma.win_log[i] = r->win_log[i];
-    ma.win_off[i] = r->win_off[i];
-    ma.word_off[i] = r->word_off[i];
-  }
-  ma.seg_per_bd = r->seg_per_bd;
-  ma.word_per_bd = r->word_per_bd;
-  rc = launch_match_into(r);
+  rc = j.upload(st);
   if (rc) {
     release(r);
     return rc;
   }
+  VK_TRY(cudaMemsetAsync(j.d_keys, 0, j.keys_bytes_per_dm() * j.dm_chunk, st), "memset peaks");
+  VK_TRY(j.enqueue_prep(st, &r->n_launch), "prep kernels");
+  VK_TRY(cudaEventRecord(r->ev[2], st), "event");
+
+  // a4-a7: persistent CTAs over the segment's (baseline, DM, tile, residue) units
+  int fold = 0;
+  if (const char* f = std::getenv("VOLKS_SEARCH_FOLD")) fold = std::atoi(f);
+  const vk::SearchVariant v = vk::default_variant(j.n_f, fold);
+  vk::Batch b;
+  std::memset(&b, 0, sizeof b);
+  b.d[0] = j.desc(0);
+  b.n_desc = 1;
+  b.total = vk::search_units(b.d[0], v);
+  const char* pe = std::getenv("VOLKS_SEARCH_PERSISTENT");
+  const bool persistent = !(pe && pe[0] == '0');
+  int grid = 0;
+  if (persistent) {
+    VK_TRY(cudaMallocAsync(reinterpret_cast<void**>(&r->counter), sizeof(unsigned long long), st),
+           "alloc work counter");
+    VK_TRY(cudaMemsetAsync(r->counter, 0, sizeof(unsigned long long), st), "memset counter");
+    b.counter = r->counter;
+    grid = std::max(1, vk::search_occupancy(v, prm->pad_rate)) * vk::sm_count();
+  }
+  const int before = r->n_launch;
+  VK_TRY(vk::launch_search_batch(b, v, prm->pad_rate, grid, st, &r->n_launch), "search kernel");
+  r->n_search_launch = r->n_launch - before;
+  VK_TRY(cudaEventRecord(r->ev[3], st), "event");
+
+  // a8
+  b.counter = nullptr;
+  b.total = (long long)seg->n_bl * prm->n_dm * prm->n_win;
+  VK_TRY(vk::launch_select_batch(b, st, &r->n_launch), "select kernel");
+  VK_TRY(cudaEventRecord(r->ev[4], st), "event");
+  // a9
+  b.total = (long long)seg->n_bl * prm->n_dm;
+  VK_TRY(vk::launch_match_batch(b, st, &r->n_launch), "match kernel");
   VK_TRY(cudaEventRecord(r->ev[5], st), "event");
   *out = r;
   return 0;
@@ -474,29 +540,36 @@ int volks_candidates(volks_result* r, volks_candidate* buf, size_t cap, size_t* 
   if (!r->have_cands) {
     int rc = sync_result(r);
     if (rc) return rc;
+    vk::SegJob& j = *r->job;
     unsigned int count = 0;
-    cudaError_t e = cudaMemcpy(&count, r->d_count, sizeof count, cudaMemcpyDeviceToHost);
+    cudaError_t e = cudaMemcpy(&count, j.d_count, sizeof count, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "read candidate count");
-    if (count > r->cap) {  // grow and re-run the window match only
-      cudaFreeAsync(r->d_cand, r->stream);
-      r->cap = count;
-      e = dalloc(&r->d_cand, r->cap, r->stream);
+    if (count > j.cap) {  // grow and re-run the window match only
+      if (j.n_chunks() > 1)
+        return fail(VOLKS_ENOMEM,
+                    "segment %d: %u window-matched groups exceed the buffer of %u and its earlier DM "
+                    "chunks are gone; search it again with a larger peak budget",
+                    j.seg_id, count, j.cap);
+      if (j.stream_ordered) cudaFreeAsync(j.d_cand, r->stream);
+      else cudaFree(j.d_cand);
+      j.cap = count;
+      e = j.stream_ordered
+              ? cudaMallocAsync(reinterpret_cast<void**>(&j.d_cand), j.cap * sizeof(vk::DevCand), r->stream)
+              : cudaMalloc(reinterpret_cast<void**>(&j.d_cand), j.cap * sizeof(vk::DevCand));
       if (e != cudaSuccess) return cuda_fail(e, "grow candidates");
-      r->synced = false;
-      rc = launch_match_into(r);
+      rc = vk_rerun_match(r);
+      if (!rc) rc = sync_result(r);
       if (rc) return rc;
-      rc = sync_result(r);
-      if (rc) return rc;
-      e = cudaMemcpy(&count, r->d_count, sizeof count, cudaMemcpyDeviceToHost);
+      e = cudaMemcpy(&count, j.d_count, sizeof count, cudaMemcpyDeviceToHost);
       if (e != cudaSuccess) return cuda_fail(e, "read candidate count");
     }
     std::vector<vk::DevCand> dc(count);
     if (count) {
-      e = cudaMemcpy(dc.data(), r->d_cand, count * sizeof(vk::DevCand), cudaMemcpyDeviceToHost);
+      e = cudaMemcpy(dc.data(), j.d_cand, count * sizeof(vk::DevCand), cudaMemcpyDeviceToHost);
       if (e != cudaSuccess) return cuda_fail(e, "read candidates");
     }
-    const volks_segment& s = r->seg;
-    const volks_params& p = r->prm;
+    const volks_segment& s = j.seg;
+    const volks_params& p = j.prm;
     std::vector<volks_candidate> all(count);
     for (unsigned i = 0; i < count; ++i) {
       const vk::DevCand& c = dc[i];
@@ -504,7 +577,7 @@ int volks_candidates(volks_result* r, volks_candidate* buf, size_t cap, size_t* 
       std::memset(&o, 0, sizeof o);
       const int W = 1 << c.win_log;
       const int R = (W == 1 || p.pad_rate == 0) ? 1 : p.pad_rate * W;
-      const int q = (int)(c.lin / (uint32_t)r->M), m = (int)(c.lin % (uint32_t)r->M);
+      const int q = (int)(c.lin / (uint32_t)j.M), m = (int)(c.lin % (uint32_t)j.M);
       o.bl = c.bl;
       o.dm_idx = c.dm_idx;
       o.win = W;
@@ -513,18 +586,18 @@ int volks_candidates(volks_result* r, volks_candidate* buf, size_t cap, size_t* 
       o.t1_ap = o.t0_ap + W;
       o.g0_ap = c.g0;
       o.g1_ap = c.g1;
-      o.delay_idx = m >= r->M / 2 ? m - r->M : m;
+      o.delay_idx = m >= j.M / 2 ? m - j.M : m;
       o.rate_idx = (R > 1 && q >= R / 2) ? q - R : q;
       o.n_windows = c.n_windows;
       o.peak_power = c.P;
       o.rho = c.rho;
       o.z = c.z;
       o.dm = p.dm_lo + p.dm_step * c.dm_idx;
-      o.delay_s = o.delay_idx / (r->M * s.chan_bw_mhz * 1e6);
+      o.delay_s = o.delay_idx / (j.M * s.chan_bw_mhz * 1e6);
       o.rate_hz = o.rate_idx / (R * s.t_ap_s);
     }
     // a10: cross-baseline match per DM over representative intervals
-    r->cands = cross_match(all, p.min_baselines);
+    r->cands = vk::cross_match(std::move(all), p.min_baselines);
     r->have_cands = true;
   }
   *n_total = r->cands.size();
@@ -540,7 +613,7 @@ int volks_cross_match(const volks_candidate* in, size_t n, int32_t min_baselines
   if (!n_out || (n > 0 && !in) || (cap > 0 && !out)) return fail(VOLKS_EINVAL, "NULL argument");
   if (min_baselines < 1) return fail(VOLKS_EINVAL, "min_baselines must be >= 1");
   std::vector<volks_candidate> v(in, in + n);
-  v = cross_match(std::move(v), min_baselines);
+  v = vk::cross_match(std::move(v), min_baselines);
   *n_out = v.size();
   const size_t k = std::min(cap, v.size());
   if (k) std::memcpy(out, v.data(), k * sizeof(volks_candidate));
@@ -562,9 +635,9 @@ int volks_shift_table(double f_lo_mhz, double chan_bw_mhz, int32_t n_f, double t
   p.dm_lo = dm_lo;
   p.dm_step = dm_step;
   p.n_dm = n_dm;
-  int rc = validate(&s, &p);
+  int rc = vk::validate(&s, &p);
   if (rc) return rc;
-  return shift_table(f_lo_mhz, chan_bw_mhz, n_f, t_ap_s, n_ap, dm_lo, dm_step, n_dm, shifts, nvalid);
+  return vk::shift_table(f_lo_mhz, chan_bw_mhz, n_f, t_ap_s, n_ap, dm_lo, dm_step, n_dm, shifts, nvalid);
 }
 
 int volks_result_timing(volks_result* r, volks_timing* t) {
@@ -572,6 +645,10 @@ int volks_result_timing(volks_result* r, volks_timing* t) {
   int rc = sync_result(r);
   if (rc) return rc;
   std::memset(t, 0, sizeof *t);
+  if (r->timing_valid) {
+    *t = r->timing;
+    return 0;
+  }
   float* dst[5] = {&t->ms_h2d, &t->ms_prep, &t->ms_search, &t->ms_select, &t->ms_match};
   for (int i = 0; i < 5; ++i) {
     cudaError_t e = cudaEventElapsedTime(dst[i], r->ev[i], r->ev[i + 1]);
@@ -584,53 +661,58 @@ int volks_result_timing(volks_result* r, volks_timing* t) {
 
 int volks_result_shifts(volks_result* r, int32_t* shifts, int32_t* nvalid) {
   if (!r) return fail(VOLKS_EINVAL, "NULL result");
-  if (shifts && !r->shifts.empty()) std::memcpy(shifts, r->shifts.data(), r->shifts.size() * sizeof(int32_t));
-  if (nvalid && !r->nvalid.empty()) std::memcpy(nvalid, r->nvalid.data(), r->nvalid.size() * sizeof(int32_t));
+  const vk::SegJob& j = *r->job;
+  if (shifts && !j.shifts.empty()) std::memcpy(shifts, j.shifts.data(), j.shifts.size() * sizeof(int32_t));
+  if (nvalid && !j.nvalid.empty()) std::memcpy(nvalid, j.nvalid.data(), j.nvalid.size() * sizeof(int32_t));
   return 0;
 }
 
 int volks_result_peaks(volks_result* r, int32_t bl, int32_t dm_idx, int32_t win_idx, float* P, int32_t* q,
                        int32_t* m, size_t cap, size_t* n_seg) {
   if (!r || !n_seg) return fail(VOLKS_EINVAL, "NULL argument");
-  if (bl < 0 || bl >= r->seg.n_bl || dm_idx < 0 || dm_idx >= r->prm.n_dm || win_idx < 0 ||
-      win_idx >= r->prm.n_win)
+  const vk::SegJob& j = *r->job;
+  if (bl < 0 || bl >= j.seg.n_bl || dm_idx < 0 || dm_idx >= j.prm.n_dm || win_idx < 0 || win_idx >= j.prm.n_win)
     return fail(VOLKS_EINVAL, "series index out of range");
+  const int last = j.n_chunks() - 1;
+  const int d0 = last > 0 ? last * j.dm_chunk : 0;
+  if (dm_idx < d0) return fail(VOLKS_EINVAL, "peaks of DM %d were overwritten by a later DM chunk", dm_idx);
   int rc = sync_result(r);
   if (rc) return rc;
-  const int W = 1 << r->win_log[win_idx];
-  const size_t ns = (size_t)std::max(0, r->nvalid[dm_idx]) / W;
+  const int W = 1 << j.win_log[win_idx];
+  const size_t ns = (size_t)std::max(0, j.nvalid[dm_idx]) / W;
   *n_seg = ns;
   const size_t n = std::min(ns, cap);
-  if (n == 0 || r->empty) return 0;
+  if (n == 0 || j.empty) return 0;
   std::vector<unsigned long long> k(n);
-  const size_t off = ((size_t)bl * r->prm.n_dm + dm_idx) * r->seg_per_bd + r->win_off[win_idx];
-  cudaError_t e = cudaMemcpy(k.data(), r->d_keys + off, n * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+  const int n_dm_c = std::min(j.dm_chunk, j.prm.n_dm - d0);
+  const size_t off = ((size_t)bl * n_dm_c + (dm_idx - d0)) * j.seg_per_bd + j.win_off[win_idx];
+  cudaError_t e = cudaMemcpy(k.data(), j.d_keys + off, n * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "read peaks");
   for (size_t i = 0; i < n; ++i) {
     const uint32_t hi = (uint32_t)(k[i] >> 32), lin = 0xffffffffu - (uint32_t)(k[i] & 0xffffffffu);
     float f;
     std::memcpy(&f, &hi, 4);
     if (P) P[i] = f;
-    if (q) q[i] = (int32_t)(lin / (uint32_t)r->M);
-    if (m) m[i] = (int32_t)(lin % (uint32_t)r->M);
+    if (q) q[i] = (int32_t)(lin / (uint32_t)j.M);
+    if (m) m[i] = (int32_t)(lin % (uint32_t)j.M);
   }
   return 0;
 }
 
 int volks_result_stats(volks_result* r, int32_t bl, int32_t dm_idx, int32_t win_idx, double* mean, double* sd) {
   if (!r || !mean || !sd) return fail(VOLKS_EINVAL, "NULL argument");
-  if (bl < 0 || bl >= r->seg.n_bl || dm_idx < 0 || dm_idx >= r->prm.n_dm || win_idx < 0 ||
-      win_idx >= r->prm.n_win)
+  const vk::SegJob& j = *r->job;
+  if (bl < 0 || bl >= j.seg.n_bl || dm_idx < 0 || dm_idx >= j.prm.n_dm || win_idx < 0 || win_idx >= j.prm.n_win)
     return fail(VOLKS_EINVAL, "series index out of range");
   int rc = sync_result(r);
   if (rc) return rc;
-  if (r->empty) {
+  if (j.empty) {
     *mean = *sd = 0.0;
     return 0;
   }
   double v[2];
-  const size_t off = (((size_t)bl * r->prm.n_dm + dm_idx) * r->prm.n_win + win_idx) * 2;
-  cudaError_t e = cudaMemcpy(v, r->d_stats + off, sizeof v, cudaMemcpyDeviceToHost);
+  const size_t off = (((size_t)bl * j.prm.n_dm + dm_idx) * j.prm.n_win + win_idx) * 2;
+  cudaError_t e = cudaMemcpy(v, j.d_stats + off, sizeof v, cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "read stats");
   *mean = v[0];
   *sd = v[1];
@@ -639,15 +721,16 @@ int volks_result_stats(volks_result* r, int32_t bl, int32_t dm_idx, int32_t win_
 
 int volks_result_gains(volks_result* r, float* gains, size_t cap_floats) {
   if (!r || !gains) return fail(VOLKS_EINVAL, "NULL argument");
-  const size_t n = (size_t)r->seg.n_bl * r->n_f * 2;
+  const vk::SegJob& j = *r->job;
+  const size_t n = (size_t)j.seg.n_bl * j.n_f * 2;
   if (cap_floats < n) return fail(VOLKS_EINVAL, "gains buffer holds %zu floats, need %zu", cap_floats, n);
   int rc = sync_result(r);
   if (rc) return rc;
-  if (r->empty || !r->d_gain) {
+  if (j.empty || !j.d_gain) {
     std::memset(gains, 0, n * sizeof(float));
     return 0;
   }
-  cudaError_t e = cudaMemcpy(gains, r->d_gain, n * sizeof(float), cudaMemcpyDeviceToHost);
+  cudaError_t e = cudaMemcpy(gains, j.d_gain, n * sizeof(float), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "read gains");
   return 0;
 }

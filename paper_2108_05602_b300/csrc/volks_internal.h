@@ -1,5 +1,6 @@
-// Internal declarations shared by the host driver (volks_api.cu) and the
-// kernels (volks_kernels.cu).  Not part of the ABI.
+// Internal declarations shared by the host driver (volks_api.cu,
+// volks_plan.cu, volks_noalloc.cu) and the kernels (volks_kernels.cu).
+// Not part of the ABI.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -9,6 +10,7 @@ namespace vk {
 constexpr int kTile = 32;          // APs per search tile (largest window)
 constexpr int kMaxWinLog = 5;      // windows 1, 2, 4, 8, 16, 32
 constexpr int kMaxSegPerTile = 63; // 32 + 16 + 8 + 4 + 2 + 1
+constexpr int kMaxDesc = 64;       // ranges per launch (kernel parameter block)
 
 // Window-matched group found on the device (a9), before the host's
 // cross-baseline step.
@@ -21,6 +23,49 @@ struct DevCand {
   double rho, z;
 };
 
+// One work range: one segment restricted to a contiguous chunk of its DM
+// trials.  Passed to the kernels inside a __grid_constant__ parameter block.
+struct SegDesc {
+  const float2* xn;                // [n_bl][n_f][n_ap] normalised, calibrated
+  const int32_t* shifts;           // [n_dm][n_f] of this chunk
+  const int32_t* nvalid;           // [n_dm] of this chunk
+  const float2* tw_n;              // W_{n_f}^i, i < n_f
+  const float2* tw_m;              // W_M^i, i < M
+  unsigned long long* keys;        // [n_bl][n_dm][seg_per_bd] of this chunk
+  double* stats;                   // [n_bl][n_dm_total][n_win][2] (all DMs of the segment)
+  uint32_t* bits;                  // [n_bl][n_dm][word_per_bd] of this chunk
+  DevCand* cand;                   // window-matched groups of the segment
+  unsigned int* count;
+  unsigned int cap;
+  int seg_id;
+  long long seg_per_bd, word_per_bd;
+  long long base;                  // first work unit of this range within its launch
+  int n_bl, n_ap, n_f, n_dm, n_dm_total, d0, pad_delay, M, n_tiles;
+  int n_win, n_eff, min_windows, win_mask;
+  int win_log[kMaxWinLog + 1];     // by window index
+  int win_off[kMaxWinLog + 1];     // segment offset, by window index
+  int word_off[kMaxWinLog + 1];    // bit-word offset, by window index
+  int win_off_l[kMaxWinLog + 1];   // segment offset, by log2(window)
+  double thresh;
+};
+
+// A launch over up to kMaxDesc ranges.  counter == nullptr: unit
+// blockIdx.x + unit0 per CTA (per thread for the match kernel); otherwise
+// the search kernel is persistent and pulls units from *counter (zeroed
+// before the launch) until `total`.
+struct Batch {
+  unsigned long long* counter;
+  long long total;
+  long long unit0;
+  int n_desc;
+  SegDesc d[kMaxDesc];
+};
+
+// Work split of the search kernel: 32 * n1 threads, fold band folds.
+struct SearchVariant {
+  int n1, fold;
+};
+
 struct PrepArgs {
   const float2* vis;               // [n_bl][n_ap][n_f]
   float2* xn;                      // [n_bl][n_f][n_ap]  (normalised, calibrated)
@@ -31,56 +76,45 @@ struct PrepArgs {
   int normalize, skip_first_chan;
 };
 
+// Single-range search arguments (one CTA per work unit, no counter).
 struct SearchArgs {
-  const float2* xn;                // [n_bl][n_f][n_ap]
-  const int32_t* shifts;           // [n_dm][n_f]
-  const int32_t* nvalid;           // [n_dm]
-  const float2* tw_n;              // W_N^i, i < N   (N = n_f per residue pass)
-  const float2* tw_m;              // W_M^i, i < M   (M = pad_delay * n_f)
-  unsigned long long* keys;        // [n_bl][n_dm][seg_per_bd]
+  const float2* xn;
+  const int32_t* shifts;
+  const int32_t* nvalid;
+  const float2* tw_n;
+  const float2* tw_m;
+  unsigned long long* keys;
   int n_bl, n_ap, n_f, n_dm, pad_delay, M;
-  int win_mask;                    // bit l set: window 2^l searched
-  int win_off[kMaxWinLog + 1];     // segment offset of window 2^l inside a (b, d) block
+  int win_mask;
+  int win_off[kMaxWinLog + 1];     // by log2(window)
   long long seg_per_bd;
   int n_tiles;
-  int fold;                        // n_f = 512 only: 1 = one 512-thread CTA, else two 256-thread CTAs
-};
-
-struct SelectArgs {
-  const unsigned long long* keys;
-  const int32_t* nvalid;
-  double* stats;                   // [n_bl][n_dm][n_win][2] mean, std
-  uint32_t* bits;                  // [n_bl][n_dm][word_per_bd]
-  int n_bl, n_dm, n_win, n_eff;
-  int win_log[kMaxWinLog + 1];     // log2 of window i
-  int win_off[kMaxWinLog + 1];     // segment offset of window i in a (b, d) block
-  int word_off[kMaxWinLog + 1];    // bit-word offset of window i in a (b, d) block
-  long long seg_per_bd, word_per_bd;
-  double thresh;
-};
-
-struct MatchArgs {
-  const unsigned long long* keys;
-  const double* stats;
-  const uint32_t* bits;
-  const int32_t* nvalid;
-  DevCand* out;
-  unsigned int* count;
-  unsigned int cap;
-  int n_bl, n_dm, n_win, n_eff, min_windows;
-  int win_log[kMaxWinLog + 1];
-  int win_off[kMaxWinLog + 1];
-  int word_off[kMaxWinLog + 1];
-  long long seg_per_bd, word_per_bd;
+  int fold;
 };
 
 // Set the calling thread's message returned by volks_last_error().
 void set_last_error(const char* msg);
 
+// Default work split for a band of n_f points (fold_override > 0 forces
+// that fold where a variant with it exists).
+SearchVariant default_variant(int n_f, int fold_override);
+// The variants compiled for a band of n_f points (at most 4).
+int search_variants(int n_f, SearchVariant* out);
+// Search units (CTAs) of one range.
+long long search_units(const SegDesc& d, SearchVariant v);
+// CTAs per SM of the search kernel for this variant (0 on error).
+int search_occupancy(SearchVariant v, int pad_rate);
+
 // Launchers (return the launch's cudaError_t).
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s, int* n_launch);
+// Persistent (b.counter != nullptr; grid_ctas CTAs) or one CTA per unit;
+// all ranges of b share n_f, pad_rate and the variant; b.total = units.
+cudaError_t launch_search_batch(Batch& b, SearchVariant v, int pad_rate, int grid_ctas,
+                                cudaStream_t s, int* n_launch);
+cudaError_t launch_select_batch(Batch& b, cudaStream_t s, int* n_launch);
+cudaError_t launch_match_batch(Batch& b, cudaStream_t s, int* n_launch);
+// Single-range search, one CTA per unit (used where no counter may be
+// allocated).
 cudaError_t launch_search(const SearchArgs& a, int pad_rate, cudaStream_t s, int* n_launch);
-cudaError_t launch_select(const SelectArgs& a, cudaStream_t s, int* n_launch);
-cudaError_t launch_match(const MatchArgs& a, cudaStream_t s, int* n_launch);
 
 }  // namespace vk

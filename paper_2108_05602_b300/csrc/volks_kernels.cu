@@ -11,6 +11,7 @@
 //                   windows in start order: overlap groups -> candidates
 #include <algorithm>
 #include <cstdint>
+#include <cstring>
 #include <cuda_runtime.h>
 
 #include "fft_regs.cuh"
@@ -187,50 +188,59 @@ __device__ __forceinline__ void rate_window(const float2* __restrict__ S, int c,
   }
 }
 
-// One CTA = (baseline b, DM trial d, 32-AP tile, delay residue r).  Zero
-// padding by pad_delay, with the band folded FOLD times, splits the M-point
-// delay transform (M = pad_delay * n_f) into P = pad_delay * FOLD
+// Range holding work unit u (ranges are in increasing `base` order).
+__device__ __forceinline__ int find_desc(const Batch& p, long long u) {
+  int lo = 0, hi = p.n_desc - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (p.d[mid].base <= u) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Per-unit state in shared memory: the range descriptor and the decoded
+// unit.  Fields are re-read from here after each barrier instead of being
+// kept live in registers through the FFT stages.
+struct UnitState {
+  SegDesc a;
+  int b, d, r, t0, nv, valid;
+};
+
+// One work unit = (baseline b, DM trial d, 32-AP tile, delay residue r).
+// Zero padding by pad_delay, with the band folded FOLD times, splits the
+// M-point delay transform (M = pad_delay * n_f) into P = pad_delay * FOLD
 // independent N-point FFTs, N = n_f / FOLD:
 //   Y[P c + r] = sum_{k<N} W_M^{k r} (sum_{f<FOLD} X[k + N f] W_P^{f r}) W_N^{k c},
-// so a CTA computes the delay cells m = P c + r (c < N) of its residue r.
+// so a unit computes the delay cells m = P c + r (c < N) of its residue r.
 // N = 32 * N1; the CTA has N threads.
 //   stage 0  lane = AP, warp owns k0 = warp*KPW + j: gather xn[k][t + shift_k],
 //            fold and pre-twiddle
 //   stage 1  N1-point FFTs over k1 (k = k0 + 32 k1), twiddle W_N^{k0 m1}
 //   stage 2  lane = AP, warp = m1: 32-point FFT over k0 -> Y[m1 + N1 m2]
 //   stage 3  thread = delay column c: rate FFTs over the tile's APs
+// Called by every thread of the CTA after `us` has been filled and
+// synchronised; returns with no barrier pending.
 template <int N1, int PADR, int FOLD>
-__global__ void __launch_bounds__(32 * N1, 16 / N1) search_kernel(const SearchArgs a, int b_base) {
+__device__ __forceinline__ void search_tile(const UnitState& us, float2* S, uint2* slot) {
   constexpr int N = 32 * N1;
   constexpr int KPW = 32 / N1;
   constexpr int LD = N + 1;
-  extern __shared__ __align__(16) float2 sm[];
-  float2* S = sm;
-  uint2* slot = reinterpret_cast<uint2*>(sm + 32 * LD);
-
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int P = a.pad_delay * FOLD;
-  long long bid = blockIdx.x;
-  const int r = (int)(bid % P);
-  bid /= P;
-  const int d = (int)(bid % a.n_dm);
-  bid /= a.n_dm;
-  const int tile = (int)(bid % a.n_tiles);
-  const int b = b_base + (int)(bid / a.n_tiles);
-  const int t0 = tile * kTile;
-  const int nv = a.nvalid[d];
-  if (t0 >= nv) return;
-
   // ---- stage 0 + 1 ----
   {
-    const float2* xb = a.xn + (size_t)b * a.n_f * a.n_ap;
-    const int32_t* sh = a.shifts + (size_t)d * a.n_f;
-    const int t = t0 + lane;
+    const SegDesc& a = us.a;
+    const int b = us.b, d = us.d, r = us.r, nv = us.nv;
+    const int n_ap = a.n_ap, n_f = a.n_f, Mm = a.M;
+    const float2* xb = a.xn + (size_t)b * n_f * n_ap;
+    const int32_t* sh = a.shifts + (size_t)d * n_f;
+    const float2* tw_m = a.tw_m;
+    const float2* tw_n = a.tw_n;
+    const int t = us.t0 + lane;
     const bool tin = t < nv;
     float2 wf[FOLD];  // W_P^{f r} = W_M^{N f r}
     static_for<0, FOLD>([&](auto ff) {
       constexpr int F = decltype(ff)::value;
-      wf[F] = F == 0 ? make_float2(1.f, 0.f) : __ldg(a.tw_m + (N * F * r) % a.M);
+      wf[F] = F == 0 ? make_float2(1.f, 0.f) : __ldg(tw_m + (N * F * r) % Mm);
     });
     static_for<0, KPW>([&](auto jj) {
       constexpr int J = decltype(jj)::value;
@@ -244,14 +254,14 @@ __global__ void __launch_bounds__(32 * N1, 16 / N1) search_kernel(const SearchAr
           constexpr int F = decltype(ff)::value;
           const int kf = k + N * F;
           float2 u = make_float2(0.f, 0.f);
-          if (tin) u = __ldg(xb + (size_t)kf * a.n_ap + t + __ldg(sh + kf));
+          if (tin) u = __ldg(xb + (size_t)kf * n_ap + t + __ldg(sh + kf));
           if constexpr (F == 0) {
             v = u;
           } else {
             v = cadd(v, cmul(u, wf[F]));
           }
         });
-        if (r != 0) v = cmul(v, __ldg(a.tw_m + (k * r) % a.M));
+        if (r != 0) v = cmul(v, __ldg(tw_m + k * r));  // k < N, r < P: k r < M
         x[K1] = v;
       });
       fft_dif<N1>(x);
@@ -259,7 +269,7 @@ __global__ void __launch_bounds__(32 * N1, 16 / N1) search_kernel(const SearchAr
         constexpr int M1 = decltype(mm1)::value;
         float2 v = x[bitrev(M1, ilog2(N1))];
         // W_N^{k0 m1} = W_{n_f}^{k0 m1 FOLD}
-        if constexpr (M1 != 0) v = cmul(v, __ldg(a.tw_n + (k0 * M1 * FOLD) % a.n_f));
+        if constexpr (M1 != 0) v = cmul(v, __ldg(tw_n + k0 * M1 * FOLD));  // < 32 N1 FOLD = n_f
         S[lane * LD + k0 * N1 + M1] = v;
       });
     });
@@ -281,29 +291,37 @@ __global__ void __launch_bounds__(32 * N1, 16 / N1) search_kernel(const SearchAr
   }
   __syncthreads();
   // ---- stage 3 ----
-  const int c = threadIdx.x;
-  const uint32_t m = (uint32_t)(c * P + r);
-  const uint32_t M = (uint32_t)a.M;
+  const int win_mask = us.a.win_mask;
   // slot base of window 2^l: segments of the searched smaller windows first
   auto slot_base = [&](int l) {
     int o = 0;
     for (int i = 0; i < l; ++i)
-      if (a.win_mask & (1 << i)) o += kTile >> i;
+      if (win_mask & (1 << i)) o += kTile >> i;
     return o;
   };
-  if (a.win_mask & 1) rate_window<1, PADR, N1>(S, c, m, M, t0, nv, slot_base(0), slot, warp, lane);
-  if (a.win_mask & 2) rate_window<2, PADR, N1>(S, c, m, M, t0, nv, slot_base(1), slot, warp, lane);
-  if (a.win_mask & 4) rate_window<4, PADR, N1>(S, c, m, M, t0, nv, slot_base(2), slot, warp, lane);
-  if (a.win_mask & 8) rate_window<8, PADR, N1>(S, c, m, M, t0, nv, slot_base(3), slot, warp, lane);
-  if (a.win_mask & 16) rate_window<16, PADR, N1>(S, c, m, M, t0, nv, slot_base(4), slot, warp, lane);
-  if (a.win_mask & 32) rate_window<32, PADR, N1>(S, c, m, M, t0, nv, slot_base(5), slot, warp, lane);
+  {
+    const int c = threadIdx.x;
+    const int P = us.a.pad_delay * FOLD;
+    const uint32_t m = (uint32_t)(c * P + us.r);
+    const uint32_t M = (uint32_t)us.a.M;
+    const int t0 = us.t0, nv = us.nv;
+    if (win_mask & 1) rate_window<1, PADR, N1>(S, c, m, M, t0, nv, slot_base(0), slot, warp, lane);
+    if (win_mask & 2) rate_window<2, PADR, N1>(S, c, m, M, t0, nv, slot_base(1), slot, warp, lane);
+    if (win_mask & 4) rate_window<4, PADR, N1>(S, c, m, M, t0, nv, slot_base(2), slot, warp, lane);
+    if (win_mask & 8) rate_window<8, PADR, N1>(S, c, m, M, t0, nv, slot_base(3), slot, warp, lane);
+    if (win_mask & 16) rate_window<16, PADR, N1>(S, c, m, M, t0, nv, slot_base(4), slot, warp, lane);
+    if (win_mask & 32) rate_window<32, PADR, N1>(S, c, m, M, t0, nv, slot_base(5), slot, warp, lane);
+  }
   __syncthreads();
   // ---- merge the warps' bests and publish one key per segment ----
   const int ns = slot_base(kMaxWinLog + 1);
+  const int t0 = us.t0, nv = us.nv;
+  unsigned long long* keys =
+      us.a.keys + ((size_t)us.b * us.a.n_dm + us.d) * us.a.seg_per_bd;
   for (int i = threadIdx.x; i < ns; i += N) {
     int l = 0, base = 0;
     for (;; ++l) {
-      if (!(a.win_mask & (1 << l))) continue;
+      if (!(win_mask & (1 << l))) continue;
       if (i < base + (kTile >> l)) break;
       base += kTile >> l;
     }
@@ -321,27 +339,83 @@ __global__ void __launch_bounds__(32 * N1, 16 / N1) search_kernel(const SearchAr
       }
     }
     const unsigned long long key = ((unsigned long long)bp << 32) | (unsigned long long)(0xffffffffu - bl);
-    int woff = 0;  // a.win_off[l] without a dynamic index into the parameter block
-#pragma unroll
-    for (int i = 0; i <= kMaxWinLog; ++i)
-      if (i == l) woff = a.win_off[i];
-    atomicMax(a.keys + ((size_t)b * a.n_dm + d) * a.seg_per_bd + woff + sg, key);
+    atomicMax(keys + us.a.win_off_l[l] + sg, key);
+  }
+}
+
+// Search kernel over the ranges of a Batch: one unit per CTA, or
+// persistent CTAs pulling units from an atomic counter (dynamic load
+// balancing across ranges of different sizes).
+template <int N1, int PADR, int FOLD>
+__global__ void __launch_bounds__(32 * N1, 16 / N1) search_kernel(const __grid_constant__ Batch p) {
+  constexpr int N = 32 * N1;
+  extern __shared__ __align__(16) float2 sm[];
+  float2* S = sm;
+  uint2* slot = reinterpret_cast<uint2*>(sm + 32 * (N + 1));
+  __shared__ UnitState us;
+  __shared__ int s_desc;
+  __shared__ long long s_unit;
+  const bool persistent = p.counter != nullptr;
+  long long next = (long long)blockIdx.x + p.unit0;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const long long u = persistent ? (long long)atomicAdd(p.counter, 1ULL) : next;
+      s_unit = u;
+      s_desc = u < p.total ? find_desc(p, u) : -1;
+    }
+    __syncthreads();
+    const int di = s_desc;
+    if (di < 0) return;
+    // copy the range descriptor to shared memory (8-byte words)
+    {
+      const unsigned long long* src = reinterpret_cast<const unsigned long long*>(&p.d[di]);
+      unsigned long long* dst = reinterpret_cast<unsigned long long*>(&us.a);
+      for (int i = threadIdx.x; i < (int)(sizeof(SegDesc) / 8); i += N) dst[i] = src[i];
+    }
+    if (threadIdx.x == 0) {
+      const SegDesc& a = p.d[di];
+      long long unit = s_unit - a.base;
+      const int P = a.pad_delay * FOLD;
+      us.r = (int)(unit % P);
+      unit /= P;
+      us.d = (int)(unit % a.n_dm);
+      unit /= a.n_dm;
+      const int tile = (int)(unit % a.n_tiles);
+      us.b = (int)(unit / a.n_tiles);
+      us.t0 = tile * kTile;
+      us.nv = a.nvalid[us.d];
+      us.valid = us.t0 < us.nv;
+    }
+    __syncthreads();
+    if (us.valid) search_tile<N1, PADR, FOLD>(us, S, slot);
+    if (!persistent) return;
+    __syncthreads();
   }
 }
 
 template <int N1, int PADR, int FOLD>
-static cudaError_t launch_search_t(const SearchArgs& a, cudaStream_t s, int* n_launch) {
+static size_t search_smem() {
+  return (size_t)32 * (32 * N1 + 1) * sizeof(float2) + (size_t)kMaxSegPerTile * N1 * sizeof(uint2);
+}
+
+template <int N1, int PADR, int FOLD>
+static cudaError_t launch_search_t(Batch& b, int grid_ctas, cudaStream_t s, int* n_launch) {
   constexpr int N = 32 * N1;
-  const size_t smem = (size_t)32 * (N + 1) * sizeof(float2) + (size_t)kMaxSegPerTile * N1 * sizeof(uint2);
+  const size_t smem = search_smem<N1, PADR, FOLD>();
   cudaError_t e = cudaFuncSetAttribute(search_kernel<N1, PADR, FOLD>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const long long per_b = (long long)a.n_tiles * a.n_dm * a.pad_delay * FOLD;
+  if (b.total <= 0) return cudaSuccess;
+  if (b.counter) {
+    b.unit0 = 0;
+    search_kernel<N1, PADR, FOLD><<<(unsigned)std::max(1, grid_ctas), N, smem, s>>>(b);
+    ++*n_launch;
+    return cudaGetLastError();
+  }
   const long long max_grid = 2147483647LL;
-  const int b_chunk = (int)std::max(1LL, std::min((long long)a.n_bl, max_grid / std::max(1LL, per_b)));
-  for (int b0 = 0; b0 < a.n_bl; b0 += b_chunk) {
-    const int nb = std::min(b_chunk, a.n_bl - b0);
-    search_kernel<N1, PADR, FOLD><<<(unsigned)(per_b * nb), N, smem, s>>>(a, b0);
+  for (long long u0 = 0; u0 < b.total; u0 += max_grid) {
+    b.unit0 = u0;
+    search_kernel<N1, PADR, FOLD><<<(unsigned)std::min(max_grid, b.total - u0), N, smem, s>>>(b);
     ++*n_launch;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -349,31 +423,95 @@ static cudaError_t launch_search_t(const SearchArgs& a, cudaStream_t s, int* n_l
   return cudaSuccess;
 }
 
-// Work split of the delay transform by band size: N = n_f / FOLD points
-// per residue FFT, one thread per point.  n_f = 512 runs as one 512-thread
-// CTA per SM (a.fold = 1); a.fold = 2 selects two folded 256-thread CTAs
-// (each gathers twice the input per thread; slower on B300).
-template <int PADR>
-static cudaError_t launch_search_p(const SearchArgs& a, cudaStream_t s, int* n_launch) {
-  switch (a.n_f) {
-    case 64: return launch_search_t<2, PADR, 1>(a, s, n_launch);
-    case 128: return launch_search_t<4, PADR, 1>(a, s, n_launch);
-    case 256: return launch_search_t<8, PADR, 1>(a, s, n_launch);
-    case 512:
-      return a.fold == 2 ? launch_search_t<8, PADR, 2>(a, s, n_launch)
-                         : launch_search_t<16, PADR, 1>(a, s, n_launch);
-    case 1024: return launch_search_t<8, PADR, 4>(a, s, n_launch);
-    case 2048: return launch_search_t<8, PADR, 8>(a, s, n_launch);
-    default: return cudaErrorInvalidValue;
-  }
+template <int N1, int PADR, int FOLD>
+static int occupancy_t() {
+  int n = 0;
+  if (cudaFuncSetAttribute(search_kernel<N1, PADR, FOLD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)search_smem<N1, PADR, FOLD>()) != cudaSuccess)
+    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, search_kernel<N1, PADR, FOLD>, 32 * N1,
+                                                    search_smem<N1, PADR, FOLD>()) != cudaSuccess)
+    return 0;
+  return n;
+}
+
+// Compiled work splits: (n1, fold) with 32 * n1 * fold = n_f.
+#define VK_VARIANTS(X, PADR)                                                           \
+  X(2, PADR, 1) X(4, PADR, 1) X(8, PADR, 1) X(16, PADR, 1) X(8, PADR, 2) X(16, PADR, 2) \
+  X(8, PADR, 4) X(16, PADR, 4)
+
+int search_variants(int n_f, SearchVariant* out) {
+  int n = 0;
+#define VK_LIST(N1, PADR, FOLD) \
+  if (32 * N1 * FOLD == n_f && n < 4) out[n++] = SearchVariant{N1, FOLD};
+  VK_VARIANTS(VK_LIST, 0)
+#undef VK_LIST
+  return n;
+}
+
+SearchVariant default_variant(int n_f, int fold_override) {
+  SearchVariant v[4];
+  const int n = search_variants(n_f, v);
+  if (fold_override > 0)
+    for (int i = 0; i < n; ++i)
+      if (v[i].fold == fold_override) return v[i];
+  // fewest folds (fewest gathered inputs per thread), then the most threads
+  SearchVariant best = n > 0 ? v[0] : SearchVariant{0, 0};
+  for (int i = 1; i < n; ++i)
+    if (v[i].fold < best.fold) best = v[i];
+  return best;
+}
+
+long long search_units(const SegDesc& d, SearchVariant v) {
+  return (long long)d.n_bl * d.n_tiles * d.n_dm * d.pad_delay * v.fold;
+}
+
+int search_occupancy(SearchVariant v, int pad_rate) {
+#define VK_OCC(N1, PADR, FOLD) \
+  if (v.n1 == N1 && v.fold == FOLD && pad_rate == PADR) return occupancy_t<N1, PADR, FOLD>();
+  VK_VARIANTS(VK_OCC, 0)
+  VK_VARIANTS(VK_OCC, 4)
+#undef VK_OCC
+  return 0;
+}
+
+cudaError_t launch_search_batch(Batch& b, SearchVariant v, int pad_rate, int grid_ctas, cudaStream_t s,
+                                int* n_launch) {
+#define VK_LAUNCH(N1, PADR, FOLD)                    \
+  if (v.n1 == N1 && v.fold == FOLD && pad_rate == PADR) \
+    return launch_search_t<N1, PADR, FOLD>(b, grid_ctas, s, n_launch);
+  VK_VARIANTS(VK_LAUNCH, 0)
+  VK_VARIANTS(VK_LAUNCH, 4)
+#undef VK_LAUNCH
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_search(const SearchArgs& a, int pad_rate, cudaStream_t s, int* n_launch) {
-  switch (pad_rate) {
-    case 0: return launch_search_p<0>(a, s, n_launch);
-    case 4: return launch_search_p<4>(a, s, n_launch);
-    default: return cudaErrorInvalidValue;
-  }
+  Batch b;
+  memset(&b, 0, sizeof b);
+  SegDesc& d = b.d[0];
+  d.xn = a.xn;
+  d.shifts = a.shifts;
+  d.nvalid = a.nvalid;
+  d.tw_n = a.tw_n;
+  d.tw_m = a.tw_m;
+  d.keys = a.keys;
+  d.seg_per_bd = a.seg_per_bd;
+  d.n_bl = a.n_bl;
+  d.n_ap = a.n_ap;
+  d.n_f = a.n_f;
+  d.n_dm = a.n_dm;
+  d.n_dm_total = a.n_dm;
+  d.pad_delay = a.pad_delay;
+  d.M = a.M;
+  d.n_tiles = a.n_tiles;
+  d.win_mask = a.win_mask;
+  for (int l = 0; l <= kMaxWinLog; ++l) d.win_off_l[l] = a.win_off[l];
+  b.n_desc = 1;
+  const SearchVariant v = default_variant(a.n_f, a.fold);
+  if (v.n1 == 0) return cudaErrorInvalidValue;
+  b.total = search_units(d, v);
+  return launch_search_batch(b, v, pad_rate, 0, s, n_launch);
 }
 
 // ============================================================ select ====
@@ -401,68 +539,87 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return r;
 }
 
-__global__ void __launch_bounds__(256) select_kernel(const SelectArgs a) {
+// One CTA per (range, baseline, DM trial, window) series.
+__global__ void __launch_bounds__(256) select_kernel(const __grid_constant__ Batch p) {
   constexpr int NT = 256;
   __shared__ double red[NT];
-  long long bid = blockIdx.x;
-  const int wi = (int)(bid % a.n_win);
-  bid /= a.n_win;
-  const int d = (int)(bid % a.n_dm);
-  const int b = (int)(bid / a.n_dm);
+  const long long u = (long long)blockIdx.x + p.unit0;
+  if (u >= p.total) return;
+  const SegDesc& a = p.d[find_desc(p, u)];
+  long long ls = u - a.base;
+  const int wi = (int)(ls % a.n_win);
+  ls /= a.n_win;
+  const int d = (int)(ls % a.n_dm);
+  const int b = (int)(ls / a.n_dm);
   const int W = 1 << a.win_log[wi];
   const int nseg = max(a.nvalid[d], 0) / W;
+  const int n_eff = a.n_eff;
   const size_t bd = (size_t)b * a.n_dm + d;
   const unsigned long long* k = a.keys + bd * a.seg_per_bd + a.win_off[wi];
   double s = 0.0;
-  for (int i = threadIdx.x; i < nseg; i += NT) s += seg_rho(k[i], W, a.n_eff);
+  for (int i = threadIdx.x; i < nseg; i += NT) s += seg_rho(k[i], W, n_eff);
   const double mu = nseg > 0 ? block_sum<NT>(s, red) / (double)nseg : 0.0;
   double ss = 0.0;
   for (int i = threadIdx.x; i < nseg; i += NT) {
-    const double dv = seg_rho(k[i], W, a.n_eff) - mu;
+    const double dv = seg_rho(k[i], W, n_eff) - mu;
     ss = fma(dv, dv, ss);
   }
   const double sd = nseg > 0 ? sqrt(block_sum<NT>(ss, red) / (double)nseg) : 0.0;
   if (threadIdx.x == 0) {
-    a.stats[(bd * a.n_win + wi) * 2 + 0] = mu;
-    a.stats[(bd * a.n_win + wi) * 2 + 1] = sd;
+    double* st = a.stats + (((size_t)b * a.n_dm_total + a.d0 + d) * a.n_win + wi) * 2;
+    st[0] = mu;
+    st[1] = sd;
   }
   uint32_t* bits = a.bits + bd * a.word_per_bd + a.word_off[wi];
+  const double thresh = a.thresh;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int base = warp * 32; base < nseg; base += NT) {
     const int i = base + lane;
-    const bool sel = i < nseg && seg_z(seg_rho(k[i], W, a.n_eff), mu, sd) >= a.thresh;
+    const bool sel = i < nseg && seg_z(seg_rho(k[i], W, n_eff), mu, sd) >= thresh;
     const uint32_t w = __ballot_sync(0xffffffffu, sel);
     if (lane == 0) bits[base / 32] = w;
   }
 }
 
-cudaError_t launch_select(const SelectArgs& a, cudaStream_t s, int* n_launch) {
-  const long long n = (long long)a.n_bl * a.n_dm * a.n_win;
-  if (n == 0) return cudaSuccess;
-  select_kernel<<<(unsigned)n, 256, 0, s>>>(a);
-  ++*n_launch;
-  return cudaGetLastError();
+cudaError_t launch_select_batch(Batch& b, cudaStream_t s, int* n_launch) {
+  const long long max_grid = 2147483647LL;
+  for (long long u0 = 0; u0 < b.total; u0 += max_grid) {
+    b.unit0 = u0;
+    select_kernel<<<(unsigned)std::min(max_grid, b.total - u0), 256, 0, s>>>(b);
+    ++*n_launch;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 // ============================================================= match ====
-// One thread per (baseline, DM): merge the selected segments of all windows
-// in order of start AP and sweep overlap groups.
-__global__ void __launch_bounds__(128) match_kernel(const MatchArgs a) {
-  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (id >= (long long)a.n_bl * a.n_dm) return;
-  const int d = (int)(id % a.n_dm), b = (int)(id / a.n_dm);
+// One thread per (range, baseline, DM trial): merge the selected segments
+// of all windows in order of start AP and sweep overlap groups.
+__global__ void __launch_bounds__(128) match_kernel(const __grid_constant__ Batch p) {
+  const long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x + p.unit0;
+  if (u >= p.total) return;
+  const SegDesc& a = p.d[find_desc(p, u)];
+  const long long lu = u - a.base;
+  const int d = (int)(lu % a.n_dm), b = (int)(lu / a.n_dm);
   const int nv = max(a.nvalid[d], 0);
   const size_t bd = (size_t)b * a.n_dm + d;
   const uint32_t* bits = a.bits + bd * a.word_per_bd;
   const unsigned long long* keys = a.keys + bd * a.seg_per_bd;
+  const int n_win = a.n_win, n_eff = a.n_eff;
+  int wlog[kMaxWinLog + 1], woff[kMaxWinLog + 1], wdoff[kMaxWinLog + 1];
   uint32_t cur[kMaxWinLog + 1];
   int wordi[kMaxWinLog + 1], nwords[kMaxWinLog + 1];
-  for (int wi = 0; wi < a.n_win; ++wi) {
-    const int nseg = nv >> a.win_log[wi];
+  for (int wi = 0; wi < n_win; ++wi) {
+    wlog[wi] = a.win_log[wi];
+    woff[wi] = a.win_off[wi];
+    wdoff[wi] = a.word_off[wi];
+    const int nseg = nv >> wlog[wi];
     nwords[wi] = (nseg + 31) / 32;
     wordi[wi] = 0;
-    cur[wi] = nwords[wi] > 0 ? bits[a.word_off[wi]] : 0u;
+    cur[wi] = nwords[wi] > 0 ? bits[wdoff[wi]] : 0u;
   }
+  const double* stats = a.stats + ((size_t)b * a.n_dm_total + a.d0 + d) * n_win * 2;
   int g0 = 0, g1 = 0, mask = 0;
   int rw = 0, rs = 0;
   double rz = 0.0, rrho = 0.0;
@@ -473,8 +630,8 @@ __global__ void __launch_bounds__(128) match_kernel(const MatchArgs a) {
       if (o < a.cap) {
         DevCand c;
         c.bl = b;
-        c.dm_idx = d;
-        c.win_log = a.win_log[rw];
+        c.dm_idx = a.d0 + d;
+        c.win_log = wlog[rw];
         c.seg = rs;
         c.g0 = g0;
         c.g1 = g1;
@@ -484,20 +641,20 @@ __global__ void __launch_bounds__(128) match_kernel(const MatchArgs a) {
         c._pad = 0.f;
         c.rho = rrho;
         c.z = rz;
-        a.out[o] = c;
+        a.cand[o] = c;
       }
     }
   };
   for (;;) {
     int bw = -1, bstart = 0x7fffffff, bsg = 0;
-    for (int wi = 0; wi < a.n_win; ++wi) {
+    for (int wi = 0; wi < n_win; ++wi) {
       while (cur[wi] == 0u && wordi[wi] + 1 < nwords[wi]) {
         ++wordi[wi];
-        cur[wi] = bits[a.word_off[wi] + wordi[wi]];
+        cur[wi] = bits[wdoff[wi] + wordi[wi]];
       }
       if (cur[wi] != 0u) {
         const int sg = wordi[wi] * 32 + __ffs(cur[wi]) - 1;
-        const int st = sg << a.win_log[wi];
+        const int st = sg << wlog[wi];
         if (st < bstart) {
           bstart = st;
           bw = wi;
@@ -507,16 +664,15 @@ __global__ void __launch_bounds__(128) match_kernel(const MatchArgs a) {
     }
     if (bw < 0) break;
     cur[bw] &= cur[bw] - 1u;
-    const int W = 1 << a.win_log[bw];
+    const int W = 1 << wlog[bw];
     const int end = bstart + W;
-    const unsigned long long key = keys[a.win_off[bw] + bsg];
-    const double rho = seg_rho(key, W, a.n_eff);
-    const double* st = a.stats + (bd * a.n_win + bw) * 2;
-    const double z = seg_z(rho, st[0], st[1]);
+    const unsigned long long key = keys[woff[bw] + bsg];
+    const double rho = seg_rho(key, W, n_eff);
+    const double z = seg_z(rho, stats[bw * 2], stats[bw * 2 + 1]);
     if (mask != 0 && bstart < g1) {
       g1 = max(g1, end);
       mask |= 1 << bw;
-      const int RW = 1 << a.win_log[rw];
+      const int RW = 1 << wlog[rw];
       if (z > rz || (z == rz && (W < RW || (W == RW && bsg < rs)))) {
         rz = z; rrho = rho; rw = bw; rs = bsg; rkey = key;
       }
@@ -531,12 +687,17 @@ __global__ void __launch_bounds__(128) match_kernel(const MatchArgs a) {
   flush();
 }
 
-cudaError_t launch_match(const MatchArgs& a, cudaStream_t s, int* n_launch) {
-  const long long n = (long long)a.n_bl * a.n_dm;
-  if (n == 0) return cudaSuccess;
-  match_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(a);
-  ++*n_launch;
-  return cudaGetLastError();
+cudaError_t launch_match_batch(Batch& b, cudaStream_t s, int* n_launch) {
+  const long long per = 2147483647LL * 128;
+  for (long long u0 = 0; u0 < b.total; u0 += per) {
+    b.unit0 = u0;
+    const long long n = std::min(per, b.total - u0);
+    match_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(b);
+    ++*n_launch;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace vk

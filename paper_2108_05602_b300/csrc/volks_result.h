@@ -1,0 +1,28 @@
+// The opaque volks_result of include/volks.h: a view of one segment's
+// search (owned by the handle for volks_search_segment, borrowed from the
+// plan for volks_plan_result).
+#pragma once
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/volks.h"
+#include "volks_job.h"
+
+struct volks_result {
+  vk::SegJob* job = nullptr;          // the segment's state
+  vk::SegJob* own_job = nullptr;      // non-null when this handle owns it
+  bool borrowed = false;              // plan results: volks_free is a no-op
+  cudaStream_t stream = nullptr;      // stream of the last launch touching it
+  cudaEvent_t ev[6] = {};
+  unsigned long long* counter = nullptr;
+  int n_launch = 0, n_search_launch = 0;
+  bool synced = false, have_cands = false;
+  bool timing_valid = false;          // plan results: `timing` holds the plan's run
+  volks_timing timing{};
+  std::vector<volks_candidate> cands;
+};
+
+// Re-run the window match of a single-chunk job into its (regrown)
+// candidate buffer on r->stream.
+int vk_rerun_match(volks_result* r);
