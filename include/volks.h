@@ -213,6 +213,51 @@ int volks_result_stats(volks_result *res, int32_t bl, int32_t dm_idx,
  * divided by the channel RMS) applied before dedispersion. */
 int volks_result_gains(volks_result *res, float *gains, size_t cap_floats);
 
+/* ---- batch plans --------------------------------------------------------
+ *
+ * A plan searches many segments of different shapes (baselines, APs, IFs,
+ * channels, DM grids, windows) together: the per-(baseline, DM, tile,
+ * residue) work of all segments of one band class (n_f, pad_rate) is done
+ * by one persistent search launch whose CTAs pull work from a shared
+ * counter, followed by one select and one match launch over all segments.
+ * Results are those of volks_search_segment on each segment.
+ *
+ * volks_plan_create: validates every (segment, params) pair; visibilities
+ *   must be device memory.  peak_budget_bytes > 0 bounds the per-trial peak
+ *   buffers (8 bytes per trial) of the whole plan: segments whose peaks do
+ *   not fit are processed in DM chunks (rounds), reusing their buffers;
+ *   <= 0 keeps all DMs resident.  flags: VOLKS_PLAN_AUTOTUNE times the
+ *   compiled work splits of each band class on the plan's own data and
+ *   keeps the fastest (cached per process); VOLKS_PLAN_GRAPH captures a run
+ *   into one CUDA graph, replayed by every volks_plan_run with the same
+ *   visibility pointers.  Allocates all device memory (cudaMalloc) here.
+ * volks_plan_run: enqueue one run on `cuda_stream`; vis = n device pointers
+ *   of new visibilities of the same shapes, or NULL to reuse the previous
+ *   ones.  A changed pointer re-captures the graph.  Waits for the plan's
+ *   previous run if it was on another stream.
+ * volks_plan_result: borrowed handle of segment i (valid until
+ *   volks_plan_free; volks_free on it does nothing).  volks_candidates,
+ *   volks_result_peaks/_stats/_gains/_shifts/_timing work on it and refer
+ *   to the last run.  Peaks are readable only for the DMs of a segment's
+ *   last chunk.
+ * volks_plan_timing: device time of the last run: ms_search = the search
+ *   launches, ms_select = everything else (prep, select, match, clears).
+ */
+#define VOLKS_PLAN_AUTOTUNE 1
+#define VOLKS_PLAN_GRAPH 2
+
+typedef struct volks_plan volks_plan;
+
+int volks_plan_create(const volks_segment *segs, const volks_params *prms, int32_t n,
+                      int64_t peak_budget_bytes, int32_t flags, volks_plan **out);
+int volks_plan_run(volks_plan *plan, const void *const *vis, void *cuda_stream);
+int volks_plan_result(volks_plan *plan, int32_t i, volks_result **res);
+int volks_plan_timing(volks_plan *plan, volks_timing *t);
+/* Rounds (DM chunks) per run, device bytes held, search launches per run. */
+int volks_plan_info(volks_plan *plan, int32_t *n_rounds, int64_t *device_bytes,
+                    int32_t *n_search_launches_per_run);
+void volks_plan_free(volks_plan *plan);
+
 /* ---- no-allocation variant ---------------------------------------------
  *
  * The paper has no counterpart to this entry point; it exists for callers

@@ -645,10 +645,7 @@ int volks_result_timing(volks_result* r, volks_timing* t) {
   int rc = sync_result(r);
   if (rc) return rc;
   std::memset(t, 0, sizeof *t);
-  if (r->timing_valid) {
-    *t = r->timing;
-    return 0;
-  }
+  if (r->plan) return vk_plan_timing(r->plan, t);
   float* dst[5] = {&t->ms_h2d, &t->ms_prep, &t->ms_search, &t->ms_select, &t->ms_match};
   for (int i = 0; i < 5; ++i) {
     cudaError_t e = cudaEventElapsedTime(dst[i], r->ev[i], r->ev[i + 1]);

@@ -11,6 +11,7 @@
 
 struct volks_result {
   vk::SegJob* job = nullptr;          // the segment's state
+  volks_plan* plan = nullptr;         // plan results: the owning plan
   vk::SegJob* own_job = nullptr;      // non-null when this handle owns it
   bool borrowed = false;              // plan results: volks_free is a no-op
   cudaStream_t stream = nullptr;      // stream of the last launch touching it
@@ -18,10 +19,11 @@ struct volks_result {
   unsigned long long* counter = nullptr;
   int n_launch = 0, n_search_launch = 0;
   bool synced = false, have_cands = false;
-  bool timing_valid = false;          // plan results: `timing` holds the plan's run
-  volks_timing timing{};
   std::vector<volks_candidate> cands;
 };
+
+// Stage times of a plan's last run.
+int vk_plan_timing(volks_plan* p, volks_timing* t);
 
 // Re-run the window match of a single-chunk job into its (regrown)
 // candidate buffer on r->stream.

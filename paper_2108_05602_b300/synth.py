@@ -280,3 +280,63 @@ def gen_evn_torch(seed: int = 2, device: str = "cuda", wl: Optional[Workload] = 
             extra = torch.randn(shp + (2,), generator=g, device=device) * sig
             vis[b, ts, ks] += torch.view_as_complex(extra)
     return wl, vis, cal, pulses
+
+
+def batch_workloads(seed: int = 3, n_seg: int = 64, dur_s=(5.0, 10.0), max_dm_trials: int = 200):
+    """Heterogeneous segments for batched searches: stations U{3..10}
+    (3-45 baselines), IFs {4, 8, 16} x channels {16, 32, 64, 128} per IF of
+    16 or 32 MHz centred on 1.6 GHz, duration U[dur_s] s of 1.024 ms APs,
+    DM range [0, U(200, 2000)] sampled with at most max_dm_trials trials
+    (step >= 2), windows 1..32."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_seg):
+        n_st = int(rng.integers(3, 11))
+        n_if = int(rng.choice([4, 8, 16]))
+        n_chan = int(rng.choice([16, 32, 64, 128]))
+        if_bw = float(rng.choice([16.0, 32.0]))
+        bw = if_bw / n_chan
+        n_ap = int(rng.uniform(*dur_s) / 1.024e-3)
+        dm_hi = float(rng.uniform(200.0, 2000.0))
+        step = max(2.0, dm_hi / max_dm_trials)
+        out.append(Workload(f"seg{i}", n_bl=n_st * (n_st - 1) // 2, n_ap=n_ap, n_if=n_if,
+                            n_chan=n_chan, t_ap_s=1.024e-3,
+                            f_lo_mhz=1600.0 - n_if * if_bw / 2, chan_bw_mhz=bw,
+                            dm_lo=0.0, dm_step=step, n_dm=int(dm_hi // step) + 1,
+                            windows=(1, 2, 4, 8, 16, 32)))
+    return out
+
+
+def gen_segment_torch(wl: Workload, seed: int, device: str = "cuda", n_pulses: int = 3):
+    """One segment drawn into device memory: torch Philox noise, the
+    calibration table and a few pulses (DM within the segment's grid, width
+    1..16 AP, SNR 8..25) at random arrival APs."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    vis = torch.view_as_complex(torch.randn((wl.n_bl, wl.n_ap, wl.n_f, 2), generator=g,
+                                            device=device, dtype=torch.float32))
+    rng = np.random.default_rng(seed)
+    cal = draw_calibration(wl, rng)
+    M = wl.pad_delay * wl.n_f
+    cell = 1.0 / (M * wl.chan_bw_mhz * 1e6)
+    pulses = []
+    k = np.arange(wl.n_f)
+    for _ in range(n_pulses):
+        dm = float(rng.uniform(wl.dm_lo, wl.dm_lo + wl.dm_step * (wl.n_dm - 1)))
+        W = int(rng.integers(1, 17))
+        sweep = int(arrival_offsets_ap(wl, dm).max())
+        if wl.n_ap - sweep - W - 1 <= 1:
+            continue
+        p = Pulse(dm=dm, t0_ap=int(rng.integers(0, wl.n_ap - sweep - W - 1)), width_ap=W,
+                  snr=float(rng.uniform(8.0, 25.0)),
+                  tau_s=rng.integers(-M // 8, M // 8, size=wl.n_bl) * cell,
+                  nu_hz=rng.uniform(-5.0, 5.0, size=wl.n_bl))
+        rows, val = pulse_footprint(wl, cal, p)
+        r = torch.as_tensor(rows.reshape(-1), device=device)
+        kk = torch.as_tensor(np.broadcast_to(k[:, None], rows.shape).reshape(-1), device=device)
+        for b in range(wl.n_bl):
+            vis[b].index_put_((r, kk), torch.as_tensor(val[b].reshape(-1).astype(np.complex64),
+                                                       device=device), accumulate=True)
+        pulses.append(p)
+    return vis, cal, pulses

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libvolks.so")
 
 VOLKS_OK, VOLKS_EINVAL, VOLKS_ENOMEM, VOLKS_ETIMEOUT, VOLKS_ECUDA = 0, -1, -2, -3, -4
 VOLKS_FP32 = 0
+VOLKS_PLAN_AUTOTUNE, VOLKS_PLAN_GRAPH = 1, 2
 
 
 class volks_segment(C.Structure):
@@ -94,6 +95,19 @@ def lib() -> C.CDLL:
     L.volks_result_stats.restype = C.c_int
     L.volks_result_gains.argtypes = [P, C.POINTER(C.c_float), SZ]
     L.volks_result_gains.restype = C.c_int
+    L.volks_plan_create.argtypes = [C.POINTER(volks_segment), C.POINTER(volks_params), I32,
+                                    C.c_int64, I32, C.POINTER(P)]
+    L.volks_plan_create.restype = C.c_int
+    L.volks_plan_run.argtypes = [P, C.POINTER(P), P]
+    L.volks_plan_run.restype = C.c_int
+    L.volks_plan_result.argtypes = [P, I32, C.POINTER(P)]
+    L.volks_plan_result.restype = C.c_int
+    L.volks_plan_timing.argtypes = [P, C.POINTER(volks_timing)]
+    L.volks_plan_timing.restype = C.c_int
+    L.volks_plan_info.argtypes = [P, C.POINTER(I32), C.POINTER(C.c_int64), C.POINTER(I32)]
+    L.volks_plan_info.restype = C.c_int
+    L.volks_plan_free.argtypes = [P]
+    L.volks_plan_free.restype = None
     L.volks_cross_match.argtypes = [C.POINTER(volks_candidate), SZ, I32,
                                     C.POINTER(volks_candidate), SZ, C.POINTER(SZ)]
     L.volks_cross_match.restype = C.c_int
@@ -225,6 +239,7 @@ class Search:
                    else self._cal.ctypes.data_as(C.POINTER(C.c_double)))
         self.seg, self.prm = seg, make_params(wl, **over)
         self.n_f = wl.n_if * wl.n_chan
+        self.n_bl = seg.n_bl
         self.handle = volks_search_segment(seg, self.prm, stream)
 
     def candidates(self) -> List[dict]:
@@ -263,14 +278,90 @@ class Search:
         return mu.value, sd.value
 
     def gains(self) -> np.ndarray:
-        g = np.zeros((self.seg.n_bl, self.n_f, 2), dtype=np.float32)
+        g = np.zeros((self.n_bl, self.n_f, 2), dtype=np.float32)
         _check(lib().volks_result_gains(C.c_void_p(self.handle),
                                         g.ctypes.data_as(C.POINTER(C.c_float)), g.size), "gains")
         return g[..., 0] + 1j * g[..., 1]
 
     def close(self):
-        if getattr(self, "handle", None):
+        if getattr(self, "handle", None) and not getattr(self, "borrowed", False):
             volks_free(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Plan:
+    """Batch plan over many segments (volks_plan_* in include/volks.h).
+
+    `items` is a list of (workload, vis device tensor, cal) triples; keyword
+    overrides apply to every segment's parameters."""
+
+    def __init__(self, items, peak_budget_bytes: int = 0, autotune: bool = True,
+                 graph: bool = True, **over):
+        n = len(items)
+        self._keep = []
+        segs = (volks_segment * n)()
+        prms = (volks_params * n)()
+        for i, (wl, vis, cal) in enumerate(items):
+            ptr, keep = _vis_pointer(vis)
+            calc = None if cal is None else np.ascontiguousarray(cal, dtype=np.float64)
+            self._keep += [keep, calc]
+            s = segs[i]
+            s.n_bl, s.n_ap, s.n_if, s.n_chan = wl.n_bl, wl.n_ap, wl.n_if, wl.n_chan
+            s.t_ap_s, s.f_lo_mhz, s.chan_bw_mhz = wl.t_ap_s, wl.f_lo_mhz, wl.chan_bw_mhz
+            s.vis = ptr
+            s.cal = None if calc is None else calc.ctypes.data_as(C.POINTER(C.c_double))
+            prms[i] = make_params(wl, **over)
+        self.n = n
+        self.n_f = [wl.n_if * wl.n_chan for wl, _, _ in items]
+        self.n_bl = [wl.n_bl for wl, _, _ in items]
+        self.prms = prms
+        flags = (VOLKS_PLAN_AUTOTUNE if autotune else 0) | (VOLKS_PLAN_GRAPH if graph else 0)
+        out = C.c_void_p()
+        _check(lib().volks_plan_create(segs, prms, n, int(peak_budget_bytes), flags,
+                                       C.byref(out)), "volks_plan_create")
+        self.handle = out.value
+
+    def run(self, vis=None, stream: int = 0):
+        arr = None
+        if vis is not None:
+            ptrs = []
+            for v in vis:
+                p, keep = _vis_pointer(v)
+                self._keep.append(keep)
+                ptrs.append(p)
+            arr = (C.c_void_p * self.n)(*ptrs)
+        _check(lib().volks_plan_run(C.c_void_p(self.handle), arr, C.c_void_p(stream)),
+               "volks_plan_run")
+
+    def result(self, i: int) -> "Search":
+        h = C.c_void_p()
+        _check(lib().volks_plan_result(C.c_void_p(self.handle), i, C.byref(h)),
+               "volks_plan_result")
+        r = Search.__new__(Search)
+        r.handle, r.prm, r.n_f, r.borrowed = h.value, self.prms[i], self.n_f[i], True
+        r.seg, r.n_bl = None, self.n_bl[i]
+        return r
+
+    def timing(self) -> volks_timing:
+        t = volks_timing()
+        _check(lib().volks_plan_timing(C.c_void_p(self.handle), C.byref(t)), "plan timing")
+        return t
+
+    def info(self):
+        r, b, s = C.c_int32(), C.c_int64(), C.c_int32()
+        _check(lib().volks_plan_info(C.c_void_p(self.handle), C.byref(r), C.byref(b),
+                                     C.byref(s)), "plan info")
+        return {"rounds": r.value, "device_bytes": b.value, "search_launches": s.value}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().volks_plan_free(C.c_void_p(self.handle))
             self.handle = None
 
     def __del__(self):
