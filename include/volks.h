@@ -258,6 +258,73 @@ int volks_plan_info(volks_plan *plan, int32_t *n_rounds, int64_t *device_bytes,
                     int32_t *n_search_launches_per_run);
 void volks_plan_free(volks_plan *plan);
 
+/* ---- request server (continuous batching) --------------------------------
+ *
+ * volks_server_submit queues a scan segment and returns at once.  A
+ * scheduler thread admits queued requests in arrival order while one of
+ * max_inflight slots (CUDA streams) is free and the request's device bytes
+ * fit the remaining hbm_budget_bytes; each admitted search runs on its own
+ * stream, so requests that arrive while others run share the device.  A
+ * request that does not fit the budget waits at the head of the queue; one
+ * whose stream's previous segment is still running is passed over.
+ *
+ * stream_id >= 0 chains segments of one observation: the server keeps, in
+ * device memory, the last H APs of the stream's previous segment (H = the
+ * largest dispersion shift of the stream's DM grid) and searches [halo |
+ * segment], so pulses crossing a segment boundary are searched whole; the
+ * candidates' AP indices then count from the start of that extended input,
+ * which begins at stream AP volks_request_info.ap_offset.  All segments of
+ * a stream need the same n_bl and n_f, at least H APs and no larger sweep.
+ * stream_id < 0: the segment is searched alone.
+ *
+ * vis (host or device) must stay valid until the request is collected;
+ * cal is copied at submission.  volks_server_wait blocks up to timeout_ms
+ * (VOLKS_ETIMEOUT after that), then returns the candidates and removes the
+ * request.  A request larger than the whole budget is refused at
+ * submission (VOLKS_ENOMEM); a request whose search fails is reported by
+ * volks_server_wait with its error.  fail_every > 0 makes every
+ * fail_every-th admission fail with VOLKS_ENOMEM before it touches the
+ * device (host-side fault injection for tests).
+ */
+typedef struct {
+  int32_t max_inflight;       /* concurrent requests on the device, 1..64 */
+  int32_t fail_every;         /* 0: off */
+  int64_t hbm_budget_bytes;   /* admission budget for request scratch */
+} volks_server_config;
+
+typedef struct {
+  int32_t status;             /* 0 done, < 0 VOLKS_E* */
+  int32_t _pad;
+  double queue_ms;            /* submit -> admission */
+  double latency_ms;          /* submit -> candidates ready on the host */
+  int64_t device_bytes;       /* budget charged */
+  int64_t ap_offset;          /* stream AP index of the searched input's AP 0 */
+  int64_t trials;
+} volks_request_info;
+
+typedef struct {
+  int64_t submitted, completed, failed;
+  int32_t queued, inflight, peak_inflight, _pad;
+  int64_t bytes_in_use, peak_bytes;
+  double p50_ms, p99_ms, mean_ms;   /* latency of completed requests */
+  int64_t trials;                   /* trials of completed requests */
+  double trials_per_s;              /* over first submission .. last completion */
+} volks_server_stats;
+
+typedef struct volks_server volks_server;
+
+int volks_server_create(const volks_server_config *cfg, volks_server **out);
+int volks_server_submit(volks_server *srv, const volks_segment *seg, const volks_params *prm,
+                        int64_t stream_id, uint64_t *request_id);
+int volks_server_wait(volks_server *srv, uint64_t request_id, int32_t timeout_ms,
+                      volks_candidate *buf, size_t cap, size_t *n_total,
+                      volks_request_info *info);
+int volks_server_get_stats(volks_server *srv, volks_server_stats *stats);
+/* Wait (up to timeout_ms) until no request is queued or running. */
+int volks_server_drain(volks_server *srv, int32_t timeout_ms);
+/* Stops admitting, waits for running requests, frees everything. */
+void volks_server_free(volks_server *srv);
+
 /* ---- no-allocation variant ---------------------------------------------
  *
  * The paper has no counterpart to this entry point; it exists for callers

@@ -12,7 +12,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libvolks.so")
-SOURCES = ["volks_kernels.cu", "volks_api.cu", "volks_plan.cu", "volks_noalloc.cu"]
+SOURCES = ["volks_kernels.cu", "volks_api.cu", "volks_plan.cu", "volks_server.cu", "volks_noalloc.cu"]
 HEADERS = ["fft_regs.cuh", "twiddle_ce.h", "volks_internal.h", "volks_job.h", "volks_result.h",
            os.path.join("..", "..", "include", "volks.h")]
 

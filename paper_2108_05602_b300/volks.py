@@ -56,6 +56,25 @@ class volks_timing(C.Structure):
                 ("n_launches", C.c_int32), ("n_search_launches", C.c_int32)]
 
 
+class volks_server_config(C.Structure):
+    _fields_ = [("max_inflight", C.c_int32), ("fail_every", C.c_int32),
+                ("hbm_budget_bytes", C.c_int64)]
+
+
+class volks_request_info(C.Structure):
+    _fields_ = [("status", C.c_int32), ("_pad", C.c_int32), ("queue_ms", C.c_double),
+                ("latency_ms", C.c_double), ("device_bytes", C.c_int64),
+                ("ap_offset", C.c_int64), ("trials", C.c_int64)]
+
+
+class volks_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
+                ("queued", C.c_int32), ("inflight", C.c_int32), ("peak_inflight", C.c_int32),
+                ("_pad", C.c_int32), ("bytes_in_use", C.c_int64), ("peak_bytes", C.c_int64),
+                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("mean_ms", C.c_double),
+                ("trials", C.c_int64), ("trials_per_s", C.c_double)]
+
+
 _lib: Optional[C.CDLL] = None
 
 
@@ -108,6 +127,20 @@ def lib() -> C.CDLL:
     L.volks_plan_info.restype = C.c_int
     L.volks_plan_free.argtypes = [P]
     L.volks_plan_free.restype = None
+    L.volks_server_create.argtypes = [C.POINTER(volks_server_config), C.POINTER(P)]
+    L.volks_server_create.restype = C.c_int
+    L.volks_server_submit.argtypes = [P, C.POINTER(volks_segment), C.POINTER(volks_params),
+                                      C.c_int64, C.POINTER(C.c_uint64)]
+    L.volks_server_submit.restype = C.c_int
+    L.volks_server_wait.argtypes = [P, C.c_uint64, I32, C.POINTER(volks_candidate), SZ,
+                                    C.POINTER(SZ), C.POINTER(volks_request_info)]
+    L.volks_server_wait.restype = C.c_int
+    L.volks_server_get_stats.argtypes = [P, C.POINTER(volks_server_stats)]
+    L.volks_server_get_stats.restype = C.c_int
+    L.volks_server_drain.argtypes = [P, I32]
+    L.volks_server_drain.restype = C.c_int
+    L.volks_server_free.argtypes = [P]
+    L.volks_server_free.restype = None
     L.volks_cross_match.argtypes = [C.POINTER(volks_candidate), SZ, I32,
                                     C.POINTER(volks_candidate), SZ, C.POINTER(SZ)]
     L.volks_cross_match.restype = C.c_int
@@ -362,6 +395,81 @@ class Plan:
     def close(self):
         if getattr(self, "handle", None):
             lib().volks_plan_free(C.c_void_p(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request server (volks_server_* in include/volks.h)."""
+
+    def __init__(self, max_inflight: int = 4, hbm_budget_bytes: int = 64 << 30,
+                 fail_every: int = 0):
+        cfg = volks_server_config(max_inflight, fail_every, int(hbm_budget_bytes))
+        out = C.c_void_p()
+        _check(lib().volks_server_create(C.byref(cfg), C.byref(out)), "volks_server_create")
+        self.handle = out.value
+        self._keep = {}
+
+    def submit(self, wl, vis, cal=None, stream_id: int = -1, **over) -> int:
+        ptr, keep = _vis_pointer(vis)
+        calc = None if cal is None else np.ascontiguousarray(cal, dtype=np.float64)
+        seg = volks_segment(wl.n_bl, wl.n_ap, wl.n_if, wl.n_chan, wl.t_ap_s, wl.f_lo_mhz,
+                            wl.chan_bw_mhz, ptr,
+                            None if calc is None else calc.ctypes.data_as(C.POINTER(C.c_double)))
+        prm = make_params(wl, **over)
+        rid = C.c_uint64()
+        _check(lib().volks_server_submit(C.c_void_p(self.handle), C.byref(seg), C.byref(prm),
+                                         int(stream_id), C.byref(rid)), "volks_server_submit")
+        self._keep[rid.value] = keep
+        return rid.value
+
+    def wait(self, rid: int, timeout_ms: int = 600000):
+        n = C.c_size_t()
+        info = volks_request_info()
+        L = lib()
+        # first call sizes the buffer; the request is collected by the second
+        buf = (volks_candidate * 1)()
+        rc = L.volks_server_wait(C.c_void_p(self.handle), rid, timeout_ms, buf, 0, C.byref(n),
+                                 C.byref(info))
+        self._keep.pop(rid, None)
+        if rc != VOLKS_OK:
+            raise VolksError(rc, "volks_server_wait")
+        return info, n.value
+
+    def wait_all(self, rid: int, timeout_ms: int = 600000):
+        """Collect a request: (info, list of candidate dicts)."""
+        L = lib()
+        cap = 1 << 16
+        while True:
+            buf = (volks_candidate * cap)()
+            n = C.c_size_t()
+            info = volks_request_info()
+            rc = L.volks_server_wait(C.c_void_p(self.handle), rid, timeout_ms, buf, cap,
+                                     C.byref(n), C.byref(info))
+            if rc != VOLKS_OK:
+                self._keep.pop(rid, None)
+                raise VolksError(rc, "volks_server_wait")
+            self._keep.pop(rid, None)
+            if n.value <= cap:
+                return info, [buf[i].as_dict() for i in range(n.value)]
+            raise RuntimeError(f"request {rid}: {n.value} candidates exceed {cap}")
+
+    def stats(self) -> volks_server_stats:
+        st = volks_server_stats()
+        _check(lib().volks_server_get_stats(C.c_void_p(self.handle), C.byref(st)), "stats")
+        return st
+
+    def drain(self, timeout_ms: int = 600000):
+        _check(lib().volks_server_drain(C.c_void_p(self.handle), timeout_ms), "drain")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().volks_server_free(C.c_void_p(self.handle))
             self.handle = None
 
     def __del__(self):
