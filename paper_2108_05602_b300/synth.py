@@ -340,3 +340,37 @@ def gen_segment_torch(wl: Workload, seed: int, device: str = "cuda", n_pulses: i
                                                        device=device), accumulate=True)
         pulses.append(p)
     return vis, cal, pulses
+
+
+def serving_workloads(seed: int = 4, n: int = 16, dur_s=(1.0, 3.0), max_dm_trials: int = 32):
+    """Request shapes for a serving stream: stations U{3..6} (3-15
+    baselines), IFs {8, 16} x channels {32, 64, 128} of 16 MHz IFs centred
+    on 1.6 GHz, duration U[dur_s] s of 1.024 ms APs, DM range
+    [0, U(200, 1500)] with at most max_dm_trials trials (step >= 2),
+    windows 1..32."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        n_st = int(rng.integers(3, 7))
+        n_if = int(rng.choice([8, 16]))
+        n_chan = int(rng.choice([32, 64, 128]))
+        bw = 16.0 / n_chan
+        dm_hi = float(rng.uniform(200.0, 1500.0))
+        step = max(2.0, dm_hi / max_dm_trials)
+        out.append(Workload(f"req{i}", n_bl=n_st * (n_st - 1) // 2,
+                            n_ap=int(rng.uniform(*dur_s) / 1.024e-3), n_if=n_if, n_chan=n_chan,
+                            t_ap_s=1.024e-3, f_lo_mhz=1600.0 - n_if * 8.0, chan_bw_mhz=bw,
+                            dm_lo=0.0, dm_step=step, n_dm=int(dm_hi // step) + 1,
+                            windows=(1, 2, 4, 8, 16, 32)))
+    return out
+
+
+def poisson_arrivals(rate_hz: float, duration_s: float, seed: int = 5) -> np.ndarray:
+    """Arrival times (s) of a Poisson process of the given rate."""
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    while True:
+        t += float(rng.exponential(1.0 / rate_hz))
+        if t >= duration_s:
+            return np.array(out)
+        out.append(t)
