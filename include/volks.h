@@ -32,8 +32,27 @@ extern "C" {
 #define VOLKS_ETIMEOUT (-3) /* a bounded device wait gave up */
 #define VOLKS_ECUDA (-4)    /* a CUDA runtime call failed */
 
-/* Arithmetic of the delay/rate search (volks_params.precision). */
+/*
+ * Arithmetic of the delay/rate search (volks_params.precision).
+ *
+ * VOLKS_FP32: every delay and rate cell is evaluated in FP32 on the CUDA
+ * cores (register FFTs).
+ * VOLKS_BF16, VOLKS_FP16, VOLKS_FP8: the delay transform stays FP32; the
+ * fringe-rate transform of the 4..32-AP windows of a 2-D search
+ * (pad_rate 4, Sec. 2.2) is a coarse DFT-matrix GEMM on the tensor cores
+ * with operands in BF16, FP16 or FP8 E4M3 (a power-of-two scale per 32-AP
+ * tile for FP16 and FP8) and FP32 accumulation.  Per segment, the 8 delay
+ * cells with the largest coarse power are then re-evaluated in FP32 over
+ * all their rate cells, and the peak is the largest FP32 value among them;
+ * windows of 1 and 2 APs are always FP32.  A peak therefore differs from
+ * the FP32 search only when the FP32 peak's delay cell is not among those
+ * 8, which needs a near-tie at the coarse precision.  1-D searches
+ * (pad_rate 0) and bands under 256 points run FP32 whatever is asked.
+ */
 #define VOLKS_FP32 0
+#define VOLKS_BF16 1
+#define VOLKS_FP16 2
+#define VOLKS_FP8 3
 
 #define VOLKS_MAX_WIN 6     /* windows are distinct powers of two, 1..32 AP */
 
@@ -140,8 +159,11 @@ void volks_default_params(volks_params *p);
  * trial plus one normalised copy of vis) is allocated stream-ordered and
  * owned by *out.
  * Errors: VOLKS_EINVAL (bad sizes, windows, pads, NULL vis with n_bl*n_ap
- * > 0, unsupported precision), VOLKS_ENOMEM, VOLKS_ECUDA.  On error *out
- * is NULL and nothing stays enqueued that touches caller memory.
+ * > 0, unknown precision), VOLKS_ENOMEM, VOLKS_ECUDA.  On error *out
+ * is NULL and nothing stays enqueued that touches caller memory.  The
+ * tensor-core kernel bounds its waits on the tensor cores (about 2 s);
+ * if one gives up, the calls that wait for the search (volks_candidates,
+ * volks_result_*) return VOLKS_ETIMEOUT.
  */
 int volks_search_segment(const volks_segment *seg, const volks_params *prm,
                          void *cuda_stream, volks_result **out);
@@ -212,6 +234,27 @@ int volks_result_stats(volks_result *res, int32_t bl, int32_t dm_idx,
 /* Waits for the search.  Complex64 gains [n_bl][n_f] (calibration phasor
  * divided by the channel RMS) applied before dedispersion. */
 int volks_result_gains(volks_result *res, float *gains, size_t cap_floats);
+
+/*
+ * Checking aid, outside the search: one 128-delay-cell block of the
+ * tensor-core rate GEMM (Sec. 2.2 2-D search, Sec. 2.4.2 step 6 window
+ * combine) of window `win` (4, 8, 16 or 32 APs) at `precision` (VOLKS_BF16,
+ * VOLKS_FP16 or VOLKS_FP8), through the same operand builders and MMA
+ * issue as the search kernel, with operand scale 1.
+ * y:   device complex64 [32][128] (APs x delay cells).
+ * out: device float [128][256]; row c, column 8 win s + 2 q (+ 1) holds the
+ *      real (imaginary) part of sum_{u < win} y[s win + u][c]
+ *      exp(-2 pi i q u / (4 win)), q < 4 win, s < 32 / win, from y and the
+ *      DFT coefficients rounded to the operand type, accumulated in FP32.
+ * flags: VOLKS_CHECK_SKIP_MMA issues no MMA, so the kernel's bounded wait
+ *      for the tensor cores (shortened to ~0.1 s here) runs out: the call
+ *      must then return VOLKS_ETIMEOUT with the context still usable.
+ * Synchronous (waits on the legacy default stream).  VOLKS_EINVAL for a
+ * bad window, precision or flag, VOLKS_ETIMEOUT if the tensor cores did not
+ * answer within the kernel's bounded wait, VOLKS_ECUDA otherwise.
+ */
+#define VOLKS_CHECK_SKIP_MMA 1
+int volks_check_rate_gemm(const void *y, int32_t win, int32_t precision, int32_t flags, float *out);
 
 /* ---- batch plans --------------------------------------------------------
  *

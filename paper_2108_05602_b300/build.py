@@ -1,5 +1,8 @@
 """Build libvolks.so in-tree with nvcc for sm_103a (B300).
 
+Each CUDA source is compiled to an object in parallel, then linked into
+one shared library.
+
     python -m paper_2108_05602_b300.build [--verbose-ptxas]
 """
 from __future__ import annotations
@@ -8,13 +11,17 @@ import os
 import shutil
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libvolks.so")
-SOURCES = ["volks_kernels.cu", "volks_api.cu", "volks_plan.cu", "volks_server.cu", "volks_noalloc.cu"]
-HEADERS = ["fft_regs.cuh", "twiddle_ce.h", "volks_internal.h", "volks_job.h", "volks_result.h",
-           os.path.join("..", "..", "include", "volks.h")]
+OBJ = os.path.join(HERE, "_build")
+SOURCES = ["volks_kernels.cu", "volks_mma.cu", "volks_api.cu", "volks_plan.cu", "volks_server.cu",
+           "volks_noalloc.cu"]
+HEADERS = ["fft_regs.cuh", "twiddle_ce.h", "search_common.cuh", "tcgen05.cuh", "volks_internal.h",
+           "volks_job.h", "volks_result.h", os.path.join("..", "..", "include", "volks.h")]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
 def nvcc_path() -> str:
@@ -32,22 +39,32 @@ def needs_build() -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+def _compile(src: str, verbose_ptxas: bool) -> tuple[str, str]:
+    obj = os.path.join(OBJ, os.path.splitext(src)[0] + ".o")
+    cmd = [nvcc_path(), "-std=c++17", "-O3", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC",
+           "--expt-relaxed-constexpr", "-I", os.path.join(HERE, "..", "include"), "-c",
+           os.path.join(CSRC, src), "-o", obj]
+    if verbose_ptxas:
+        cmd += ["-Xptxas", "-v"]
+    res = subprocess.run(cmd, capture_output=True, text=True)
+    if res.returncode != 0:
+        raise RuntimeError(f"nvcc failed on {src}:\n" + res.stdout + res.stderr)
+    return obj, res.stdout + res.stderr
+
+
 def build(verbose_ptxas: bool = False, force: bool = False) -> str:
     if not force and not needs_build():
         return LIB
-    cmd = [nvcc_path(), "-std=c++17", "-O3", "-lineinfo",
-           "-gencode", "arch=compute_103a,code=sm_103a",
-           "-Xcompiler", "-fPIC", "-shared", "--expt-relaxed-constexpr",
-           "-I", os.path.join(HERE, "..", "include"),
-           "-o", LIB + ".tmp"]
+    os.makedirs(OBJ, exist_ok=True)
+    with ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 1)) as ex:
+        results = list(ex.map(lambda s: _compile(s, verbose_ptxas), SOURCES))
     if verbose_ptxas:
-        cmd += ["-Xptxas", "-v"]
-    cmd += [os.path.join(CSRC, s) for s in SOURCES]
+        for _, log in results:
+            sys.stderr.write(log)
+    cmd = [nvcc_path(), *ARCH, "-shared", "-o", LIB + ".tmp"] + [o for o, _ in results]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
-        raise RuntimeError("nvcc failed:\n" + res.stdout + res.stderr)
-    if verbose_ptxas:
-        sys.stderr.write(res.stdout + res.stderr)
+        raise RuntimeError("nvcc link failed:\n" + res.stdout + res.stderr)
     os.replace(LIB + ".tmp", LIB)
     return LIB
 

@@ -102,7 +102,8 @@ int validate(const volks_segment* s, const volks_params* p) {
   if (!(p->pad_delay == 1 || p->pad_delay == 2 || p->pad_delay == 4 || p->pad_delay == 8))
     return fail(VOLKS_EINVAL, "pad_delay must be 1, 2, 4 or 8");
   if (!(p->pad_rate == 0 || p->pad_rate == 4)) return fail(VOLKS_EINVAL, "pad_rate must be 0 or 4");
-  if (p->precision != VOLKS_FP32) return fail(VOLKS_EINVAL, "precision %d not available", p->precision);
+  if (p->precision < VOLKS_FP32 || p->precision > VOLKS_FP8)
+    return fail(VOLKS_EINVAL, "precision %d unknown", p->precision);
   if (!std::isfinite(p->thresh)) return fail(VOLKS_EINVAL, "thresh not finite");
   if (p->min_windows < 1 || p->min_baselines < 1)
     return fail(VOLKS_EINVAL, "min_windows and min_baselines must be >= 1");
@@ -172,6 +173,7 @@ int SegJob::init(const volks_segment& s, const volks_params& p, int chunk) {
   n_eff = n_f - (p.skip_first_chan ? s.n_if : 0);
   n_tiles = (s.n_ap + kTile - 1) / kTile;
   n_tchunk = (s.n_ap + tchunk - 1) / tchunk;
+  prec = effective_precision(n_f, p.pad_rate, p.precision);
   win_mask = 0;
   long long so = 0, wo = 0;
   for (int l = 0; l <= kMaxWinLog; ++l) win_off_l[l] = 0;
@@ -394,6 +396,12 @@ int sync_result(volks_result* r) {
   if (r->synced) return 0;
   cudaError_t e = cudaStreamSynchronize(r->stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  if (r->d_err) {
+    unsigned int flag = 0;
+    e = cudaMemcpy(&flag, r->d_err, sizeof flag, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "read error flag");
+    if (flag) return fail(VOLKS_ETIMEOUT, "the tensor-core search gave up waiting for its MMAs");
+  }
   r->synced = true;
   return 0;
 }
@@ -500,24 +508,28 @@ int volks_search_segment(const volks_segment* seg, const volks_params* prm, void
   // a4-a7: persistent CTAs over the segment's (baseline, DM, tile, residue) units
   int fold = 0;
   if (const char* f = std::getenv("VOLKS_SEARCH_FOLD")) fold = std::atoi(f);
-  const vk::SearchVariant v = vk::default_variant(j.n_f, fold);
+  const vk::SearchVariant v = vk::default_variant(j.n_f, j.prec, fold);
   vk::Batch b;
   std::memset(&b, 0, sizeof b);
   b.d[0] = j.desc(0);
   b.n_desc = 1;
   b.total = vk::search_units(b.d[0], v);
   const char* pe = std::getenv("VOLKS_SEARCH_PERSISTENT");
-  const bool persistent = !(pe && pe[0] == '0');
+  // the tensor-core kernel is always persistent
+  const bool persistent = !(pe && pe[0] == '0') || j.prec != VOLKS_FP32;
   int grid = 0;
   if (persistent) {
-    VK_TRY(cudaMallocAsync(reinterpret_cast<void**>(&r->counter), sizeof(unsigned long long), st),
+    // [0] work counter, [1] error flag of the bounded waits
+    VK_TRY(cudaMallocAsync(reinterpret_cast<void**>(&r->counter), 2 * sizeof(unsigned long long), st),
            "alloc work counter");
-    VK_TRY(cudaMemsetAsync(r->counter, 0, sizeof(unsigned long long), st), "memset counter");
+    VK_TRY(cudaMemsetAsync(r->counter, 0, 2 * sizeof(unsigned long long), st), "memset counter");
     b.counter = r->counter;
-    grid = std::max(1, vk::search_occupancy(v, prm->pad_rate)) * vk::sm_count();
+    b.err = reinterpret_cast<unsigned int*>(r->counter + 1);
+    if (j.prec != VOLKS_FP32) r->d_err = b.err;
+    grid = std::max(1, vk::search_occupancy(v, prm->pad_rate, j.prec)) * vk::sm_count();
   }
   const int before = r->n_launch;
-  VK_TRY(vk::launch_search_batch(b, v, prm->pad_rate, grid, st, &r->n_launch), "search kernel");
+  VK_TRY(vk::launch_search_batch(b, v, prm->pad_rate, j.prec, grid, st, &r->n_launch), "search kernel");
   r->n_search_launch = r->n_launch - before;
   VK_TRY(cudaEventRecord(r->ev[3], st), "event");
 
@@ -729,6 +741,37 @@ int volks_result_gains(volks_result* r, float* gains, size_t cap_floats) {
   }
   cudaError_t e = cudaMemcpy(gains, j.d_gain, n * sizeof(float), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "read gains");
+  return 0;
+}
+
+int volks_check_rate_gemm(const void* y, int32_t win, int32_t precision, int32_t flags, float* out) {
+  if (!y || !out) return fail(VOLKS_EINVAL, "NULL argument");
+  if (flags & ~VOLKS_CHECK_SKIP_MMA) return fail(VOLKS_EINVAL, "unknown flags");
+  int l = -1;
+  for (int i = 2; i <= 5; ++i)
+    if (win == (1 << i)) l = i;
+  if (l < 0) return fail(VOLKS_EINVAL, "win = %d: 4, 8, 16 or 32 only", win);
+  if (!(precision == VOLKS_BF16 || precision == VOLKS_FP16 || precision == VOLKS_FP8))
+    return fail(VOLKS_EINVAL, "precision %d has no tensor-core form", precision);
+  const int M = 128;  // W_R^x = W_128^{x 128 / R} for every R = 4 win <= 128
+  std::vector<float2> tw(M);
+  for (int i = 0; i < M; ++i) tw[i] = make_float2((float)std::cos(kTwoPi * i / M), (float)-std::sin(kTwoPi * i / M));
+  float2* d_tw = nullptr;
+  unsigned int* d_err = nullptr;
+  cudaError_t e = cudaMalloc(&d_tw, M * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMalloc(&d_err, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemcpy(d_tw, tw.data(), M * sizeof(float2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(d_err, 0, sizeof(unsigned int));
+  if (e == cudaSuccess)
+    e = vk::launch_rate_gemm_probe(static_cast<const float2*>(y), d_tw, M, l, precision,
+                                   (flags & VOLKS_CHECK_SKIP_MMA) ? 1 : 0, out, d_err, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  unsigned int flag = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&flag, d_err, sizeof flag, cudaMemcpyDeviceToHost);
+  if (d_tw) cudaFree(d_tw);
+  if (d_err) cudaFree(d_err);
+  if (e != cudaSuccess) return cuda_fail(e, "rate GEMM check");
+  if (flag) return fail(VOLKS_ETIMEOUT, "the tensor cores did not complete the MMAs");
   return 0;
 }
 

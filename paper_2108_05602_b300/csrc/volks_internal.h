@@ -55,6 +55,7 @@ struct SegDesc {
 // before the launch) until `total`.
 struct Batch {
   unsigned long long* counter;
+  unsigned int* err;               // tensor-core kernel: set non-zero if a bounded wait gave up
   long long total;
   long long unit0;
   int n_desc;
@@ -95,22 +96,40 @@ struct SearchArgs {
 // Set the calling thread's message returned by volks_last_error().
 void set_last_error(const char* msg);
 
-// Default work split for a band of n_f points (fold_override > 0 forces
-// that fold where a variant with it exists).
-SearchVariant default_variant(int n_f, int fold_override);
-// The variants compiled for a band of n_f points (at most 4).
-int search_variants(int n_f, SearchVariant* out);
+// Arithmetic of the rate search that a (n_f, pad_rate, precision) search
+// actually runs: the tensor-core kernels cover 2-D searches (pad_rate 4)
+// of bands with a tensor-core work split (n_f >= 256); everything else
+// runs the FP32 kernel (VOLKS_FP32).
+int effective_precision(int n_f, int pad_rate, int precision);
+// Default work split for a band of n_f points at an effective precision
+// (fold_override > 0 forces that fold where a variant with it exists).
+SearchVariant default_variant(int n_f, int precision, int fold_override);
+// The variants compiled for a band of n_f points at an effective precision
+// (at most 4).
+int search_variants(int n_f, int precision, SearchVariant* out);
 // Search units (CTAs) of one range.
 long long search_units(const SegDesc& d, SearchVariant v);
 // CTAs per SM of the search kernel for this variant (0 on error).
-int search_occupancy(SearchVariant v, int pad_rate);
+int search_occupancy(SearchVariant v, int pad_rate, int precision);
+// True when a tensor-core search kernel is compiled for this split.
+bool mma_supported(SearchVariant v, int pad_rate, int precision);
 
 // Launchers (return the launch's cudaError_t).
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s, int* n_launch);
 // Persistent (b.counter != nullptr; grid_ctas CTAs) or one CTA per unit;
 // all ranges of b share n_f, pad_rate and the variant; b.total = units.
-cudaError_t launch_search_batch(Batch& b, SearchVariant v, int pad_rate, int grid_ctas,
+// precision: the effective precision; reduced precisions run the
+// persistent tensor-core kernel (b.counter and b.err required).
+cudaError_t launch_search_batch(Batch& b, SearchVariant v, int pad_rate, int precision, int grid_ctas,
                                 cudaStream_t s, int* n_launch);
+cudaError_t launch_search_mma(Batch& b, SearchVariant v, int precision, int grid_ctas, cudaStream_t s,
+                              int* n_launch);
+// Checking aid: one 128-delay-cell block of the rate GEMM of window 2^l
+// (y: device complex64 [32][128], tw_m: W_M^i, i < M) -> out: device
+// float [128][256], the job's accumulator columns.  skip_mma: issue no MMA
+// so that the kernel's bounded wait runs out and sets *err.
+cudaError_t launch_rate_gemm_probe(const float2* y, const float2* tw_m, int M, int l, int precision, int skip_mma,
+                                   float* out, unsigned int* err, cudaStream_t s);
 cudaError_t launch_select_batch(Batch& b, cudaStream_t s, int* n_launch);
 cudaError_t launch_match_batch(Batch& b, cudaStream_t s, int* n_launch);
 // Single-range search, one CTA per unit (used where no counter may be

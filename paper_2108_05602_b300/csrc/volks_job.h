@@ -28,6 +28,7 @@ struct SegJob {
   volks_params prm{};
   int seg_id = 0;
   int n_f = 0, M = 0, n_eff = 0, n_tiles = 0, n_tchunk = 0, tchunk = 1024, win_mask = 0;
+  int prec = 0;              // effective precision of the rate search (effective_precision)
   int win_log[kMaxWinLog + 1] = {}, win_off[kMaxWinLog + 1] = {}, word_off[kMaxWinLog + 1] = {};
   int win_off_l[kMaxWinLog + 1] = {};
   long long seg_per_bd = 0, word_per_bd = 0;

@@ -5,7 +5,7 @@
 // Sequence of one run (stream order):
 //   per segment   a2-a3 prep launches
 //   per round c   zero the peaks of every segment that has a DM chunk c;
-//                 per band class (n_f, pad_rate): persistent search over
+//                 per band class (n_f, pad_rate, precision): persistent search over
 //                 the class's ranges (dynamic work counter); batched select
 //                 and batched match over all ranges of the round.
 // A segment's peak/bitmap buffers hold one DM chunk, sized from the plan's
@@ -31,10 +31,12 @@ struct volks_plan {
   std::vector<volks_result*> results;
   int flags = 0;
   int n_rounds = 0;
-  std::map<std::pair<int, int>, vk::SearchVariant> variant;  // (n_f, pad_rate) -> split
+  // band class (n_f, mode), mode = pad_rate | effective precision << 8
+  std::map<std::pair<int, int>, vk::SearchVariant> variant;  // class -> split
   std::map<std::pair<int, int>, int> grid;                   // persistent CTAs
-  unsigned long long* d_counters = nullptr;
+  unsigned long long* d_counters = nullptr;  // n_counters work counters + the error word
   int n_counters = 0;
+  bool any_mma = false;
   cudaStream_t work = nullptr;  // capture / autotune stream
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -53,7 +55,7 @@ using vk::cuda_fail;
 using vk::fail;
 
 std::mutex g_tune_mu;
-// autotuned split per (n_f, pad_rate, pad_delay, window mask)
+// autotuned split per (n_f, mode, pad_delay, window mask)
 std::map<std::tuple<int, int, int, int>, vk::SearchVariant> g_tuned;
 
 void destroy(volks_plan* p) {
@@ -72,6 +74,11 @@ void destroy(volks_plan* p) {
   delete p;
 }
 
+int class_mode(const vk::SegJob& j) { return j.prm.pad_rate | (j.prec << 8); }
+int mode_pad_rate(int mode) { return mode & 0xff; }
+int mode_prec(int mode) { return mode >> 8; }
+unsigned int* err_word(volks_plan* p) { return reinterpret_cast<unsigned int*>(p->d_counters + p->n_counters); }
+
 struct RangeRef {
   vk::SegJob* job;
   int chunk;
@@ -81,7 +88,7 @@ struct RangeRef {
 std::map<std::pair<int, int>, std::vector<RangeRef>> round_classes(volks_plan* p, int c) {
   std::map<std::pair<int, int>, std::vector<RangeRef>> out;
   for (auto& j : p->jobs)
-    if (c < j->n_chunks()) out[{j->n_f, j->prm.pad_rate}].push_back({j.get(), c});
+    if (c < j->n_chunks()) out[{j->n_f, class_mode(*j)}].push_back({j.get(), c});
   return out;
 }
 
@@ -129,6 +136,8 @@ int enqueue_all(volks_plan* p, cudaStream_t s) {
   p->n_search_launch = 0;
   int counter_i = 0, ev_i = 0;
   if ((e = record(p->ev_begin, s)) != cudaSuccess) return cuda_fail(e, "event");
+  if ((e = cudaMemsetAsync(err_word(p), 0, sizeof(unsigned int), s)) != cudaSuccess)
+    return cuda_fail(e, "memset error word");
   for (auto& j : p->jobs) {
     if ((e = cudaMemsetAsync(j->d_count, 0, sizeof(unsigned int), s)) != cudaSuccess)
       return cuda_fail(e, "memset count");
@@ -151,11 +160,13 @@ int enqueue_all(volks_plan* p, cudaStream_t s) {
       auto batches = make_batches(kv.second, [&](const vk::SegDesc& d) { return vk::search_units(d, v); });
       for (auto& b : batches) {
         b.counter = p->d_counters + counter_i++;
+        b.err = err_word(p);
         if ((e = cudaMemsetAsync(b.counter, 0, sizeof(unsigned long long), s)) != cudaSuccess)
           return cuda_fail(e, "memset counter");
         if ((e = record(p->ev_search[ev_i++], s)) != cudaSuccess) return cuda_fail(e, "event");
         const int before = p->n_launch;
-        e = vk::launch_search_batch(b, v, kv.first.second, p->grid[kv.first], s, &p->n_launch);
+        e = vk::launch_search_batch(b, v, mode_pad_rate(kv.first.second), mode_prec(kv.first.second),
+                                    p->grid[kv.first], s, &p->n_launch);
         if (e != cudaSuccess) return cuda_fail(e, "search kernel");
         p->n_search_launch += p->n_launch - before;
         if ((e = record(p->ev_search[ev_i++], s)) != cudaSuccess) return cuda_fail(e, "event");
@@ -201,7 +212,8 @@ int capture(volks_plan* p) {
 // clears before its search.
 int autotune(volks_plan* p, std::pair<int, int> cls, const std::vector<RangeRef>& rs) {
   vk::SearchVariant vs[4];
-  const int nv = vk::search_variants(cls.first, vs);
+  const int pr = mode_pad_rate(cls.second), prec = mode_prec(cls.second);
+  const int nv = vk::search_variants(cls.first, prec, vs);
   const vk::SegJob& j0 = *rs[0].job;
   const auto key = std::make_tuple(cls.first, cls.second, j0.prm.pad_delay, j0.win_mask);
   {
@@ -222,7 +234,7 @@ int autotune(volks_plan* p, std::pair<int, int> cls, const std::vector<RangeRef>
   double best = 1e300;
   vk::SearchVariant best_v = vs[0];
   for (int i = 0; i < nv; ++i) {
-    const int occ = vk::search_occupancy(vs[i], cls.second);
+    const int occ = vk::search_occupancy(vs[i], pr, prec);
     if (occ <= 0) continue;
     const int grid = occ * vk::sm_count();
     auto batches = make_batches(rs, [&](const vk::SegDesc& d) { return vk::search_units(d, vs[i]); });
@@ -230,12 +242,13 @@ int autotune(volks_plan* p, std::pair<int, int> cls, const std::vector<RangeRef>
     const long long units = std::min<long long>(bt.total, (long long)grid * 6);
     bt.total = units;
     bt.counter = p->d_counters;
+    bt.err = err_word(p);
     float ms_best = 1e30f;
     for (int rep = 0; rep < 3; ++rep) {
       int n = 0;
       cudaMemsetAsync(bt.counter, 0, sizeof(unsigned long long), p->work);
       cudaEventRecord(a, p->work);
-      cudaError_t e = vk::launch_search_batch(bt, vs[i], cls.second, grid, p->work, &n);
+      cudaError_t e = vk::launch_search_batch(bt, vs[i], pr, prec, grid, p->work, &n);
       cudaEventRecord(b, p->work);
       if (e != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess) {
         cudaEventDestroy(a);
@@ -351,9 +364,14 @@ int volks_plan_create(const volks_segment* segs, const volks_params* prms, int32
   }
   // counters: one per search launch
   p->n_counters = std::max(1, n_search_launches(p));
-  if ((e = cudaMalloc(&p->d_counters, p->n_counters * sizeof(unsigned long long))) != cudaSuccess) {
+  if ((e = cudaMalloc(&p->d_counters, (p->n_counters + 1) * sizeof(unsigned long long))) != cudaSuccess) {
     destroy(p);
     return cuda_fail(e, "alloc counters");
+  }
+  if ((e = cudaMemsetAsync(p->d_counters, 0, (p->n_counters + 1) * sizeof(unsigned long long), p->work)) !=
+      cudaSuccess) {
+    destroy(p);
+    return cuda_fail(e, "memset counters");
   }
   p->ev_search.resize(2 * (size_t)n_search_launches(p));
   for (auto& ev : p->ev_search)
@@ -374,13 +392,16 @@ int volks_plan_create(const volks_segment* segs, const volks_params* prms, int32
           return rc;
         }
       } else {
-        p->variant[kv.first] = vk::default_variant(kv.first.first, 0);
+        p->variant[kv.first] = vk::default_variant(kv.first.first, mode_prec(kv.first.second), 0);
       }
     }
   for (int c = 0; c < p->n_rounds; ++c)
     for (auto& kv : round_classes(p, c)) {
-      if (!p->variant.count(kv.first)) p->variant[kv.first] = vk::default_variant(kv.first.first, 0);
-      const int occ = vk::search_occupancy(p->variant[kv.first], kv.first.second);
+      if (!p->variant.count(kv.first))
+        p->variant[kv.first] = vk::default_variant(kv.first.first, mode_prec(kv.first.second), 0);
+      const int occ = vk::search_occupancy(p->variant[kv.first], mode_pad_rate(kv.first.second),
+                                           mode_prec(kv.first.second));
+      if (mode_prec(kv.first.second) != VOLKS_FP32) p->any_mma = true;
       p->grid[kv.first] = std::max(1, occ) * vk::sm_count();
     }
   if ((e = cudaStreamSynchronize(p->work)) != cudaSuccess) {
@@ -396,6 +417,7 @@ int volks_plan_create(const volks_segment* segs, const volks_params* prms, int32
     r->job = p->jobs[i].get();
     r->borrowed = true;
     r->plan = p;
+    if (p->any_mma) r->d_err = err_word(p);
     r->stream = p->work;
     r->synced = true;
     p->results.push_back(r);

@@ -17,6 +17,7 @@ struct volks_result {
   cudaStream_t stream = nullptr;      // stream of the last launch touching it
   cudaEvent_t ev[6] = {};
   unsigned long long* counter = nullptr;
+  unsigned int* d_err = nullptr;      // tensor-core search: bounded-wait error flag
   int n_launch = 0, n_search_launch = 0;
   bool synced = false, have_cands = false;
   std::vector<volks_candidate> cands;

@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libvolks.so")
 
 VOLKS_OK, VOLKS_EINVAL, VOLKS_ENOMEM, VOLKS_ETIMEOUT, VOLKS_ECUDA = 0, -1, -2, -3, -4
-VOLKS_FP32 = 0
+VOLKS_FP32, VOLKS_BF16, VOLKS_FP16, VOLKS_FP8 = 0, 1, 2, 3
 VOLKS_PLAN_AUTOTUNE, VOLKS_PLAN_GRAPH = 1, 2
 
 
@@ -147,6 +147,8 @@ def lib() -> C.CDLL:
     L.volks_search_peaks_noalloc.argtypes = [C.POINTER(volks_segment), C.POINTER(volks_params),
                                              P, P, P]
     L.volks_search_peaks_noalloc.restype = C.c_int
+    L.volks_check_rate_gemm.argtypes = [P, I32, I32, I32, P]
+    L.volks_check_rate_gemm.restype = C.c_int
     _lib = L
     return L
 
@@ -198,6 +200,17 @@ def volks_search_peaks_noalloc(seg: volks_segment, prm: volks_params, stream: in
                                             C.c_void_p(peak_power_ptr),
                                             C.c_void_p(peak_cell_ptr)),
            "volks_search_peaks_noalloc")
+
+
+VOLKS_CHECK_SKIP_MMA = 1
+
+
+def volks_check_rate_gemm(y_ptr: int, win: int, precision: int, out_ptr: int, flags: int = 0):
+    """One 128-delay-cell block of the tensor-core rate GEMM (checking aid,
+    see include/volks.h): y device complex64 [32][128] -> out device float
+    [128][256]."""
+    _check(lib().volks_check_rate_gemm(C.c_void_p(y_ptr), win, precision, flags,
+                                       C.c_void_p(out_ptr)), "volks_check_rate_gemm")
 
 
 def volks_cross_match(cands: Sequence[dict], min_baselines: int) -> List[dict]:

@@ -103,7 +103,8 @@ def _seg(**kw):
     ({}, dict(n_win=7)),
     ({}, dict(pad_delay=3)),
     ({}, dict(pad_rate=3)),
-    ({}, dict(precision=2)),
+    ({}, dict(precision=4)),
+    ({}, dict(precision=-1)),
     ({}, dict(dm_lo=-10.0)),
     ({}, dict(min_windows=0)),
     ({}, dict(normalize_chan=2)),
