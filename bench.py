@@ -38,9 +38,19 @@ SM_COUNT, FP32_LANES = 148, 128
 WORKLOADS = {
     # the EVN-scale scan the metric is quoted on
     "evn_fp32": lambda synth: synth.evn(),
-    # profiling case: one baseline of the same scan (240 MB, larger than L2), 32 DM trials
+    # the same scan with the rate transform of the 2..32-AP windows as a
+    # tensor-core DFT GEMM (BF16 / FP16 / FP8 E4M3) + FP32 top-8 refinement
+    "evn_bf16": lambda synth: synth.evn(),
+    "evn_fp16": lambda synth: synth.evn(),
+    "evn_fp8": lambda synth: synth.evn(),
+    # profiling cases: one baseline of the same scan (240 MB, larger than L2), 32 DM trials
     "evn_1bl_32dm": lambda synth: __import__("dataclasses").replace(synth.evn(), n_bl=1, n_dm=32),
+    "evn_1bl_32dm_bf16": lambda synth: __import__("dataclasses").replace(synth.evn(), n_bl=1, n_dm=32),
+    "evn_1bl_32dm_fp8": lambda synth: __import__("dataclasses").replace(synth.evn(), n_bl=1, n_dm=32),
 }
+# volks_params.precision of each workload (VOLKS_FP32 = 0, BF16 = 1, FP16 = 2, FP8 = 3)
+PRECISION = {"evn_bf16": 1, "evn_fp16": 2, "evn_fp8": 3, "evn_1bl_32dm_bf16": 1, "evn_1bl_32dm_fp8": 3}
+DTYPE = {0: "f32", 1: "bf16 rate GEMM + f32", 2: "f16 rate GEMM + f32", 3: "e4m3 rate GEMM + f32"}
 
 
 BATCH = dict(n_seg=64, dur_s=(3.0, 6.0), max_dm_trials=128)
@@ -80,9 +90,56 @@ def algorithmic_flops(wl, nvalid) -> float:
     return tot * wl.n_bl
 
 
+def mma_flops(wl, nvalid, precision) -> float:
+    """Executed tensor-core flops (2 per multiply-add, zero blocks of the
+    block-diagonal operands included) of one reduced-precision search: per
+    (baseline, DM trial, searched 32-AP tile, delay residue, 128-cell block)
+    and window w in 4..32, M = 128 rows x N columns x K of the window's
+    MMAs."""
+    if precision == 0 or wl.pad_rate != 4 or wl.n_f < 256:
+        return 0.0
+    eb = 1 if precision == 3 else 2
+    per_block = 0.0
+    for w in wl.windows:
+        if w < 2:
+            continue
+        seg_kb = 2 * w * eb
+        if seg_kb >= 32:
+            per_block += (32 // w) * 2.0 * 128 * (8 * w) * (2 * w)
+        else:
+            g = 32 // seg_kb
+            per_block += (32 // w) // g * 2.0 * 128 * (8 * w * g) * (32 // eb)
+    tiles = sum((max(int(v), 0) + 31) // 32 for v in nvalid)
+    blocks_per_tile = wl.pad_delay * wl.n_f // 128   # residues x blocks = M / 128
+    return per_block * tiles * blocks_per_tile * wl.n_bl
+
+
+def cuda_core_flops_mma(wl, nvalid) -> float:
+    """Nominal CUDA-core flops of one search on the tensor-core kernel: the
+    FP32 delay transform and the 1-AP window as in algorithmic_flops; for
+    the GEMM windows (2..32 APs), 3 per coarse |Z|^2 cell (square, add,
+    max) plus the FP32 refinement of at most 8 delay cells per segment and
+    delay-residue unit (5 R log2 R + 3 R each)."""
+    M = wl.pad_delay * wl.n_f
+    fold = max(1, wl.n_f // 512)
+    units_per_seg = wl.pad_delay * fold
+    tot = 0.0
+    for nv in nvalid:
+        nv = max(int(nv), 0)
+        tot += nv * 5.0 * M * math.log2(M)
+        for w in wl.windows:
+            ns = nv // w
+            R = 1 if w == 1 else 4 * w
+            if w == 1:
+                tot += ns * M * 3.0
+            else:
+                tot += ns * (R * M * 3.0 + 8 * units_per_seg * (5.0 * R * math.log2(R) + 3.0 * R))
+    return tot * wl.n_bl
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("volks_kernels.cu", "fft_regs.cuh", "twiddle_ce.h", "volks_internal.h"):
+    for f in ("volks_kernels.cu", "search_common.cuh", "fft_regs.cuh", "twiddle_ce.h", "volks_internal.h"):
         with open(os.path.join(ROOT, "paper_2108_05602_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -244,6 +301,7 @@ def run_volks(args):
     B.build()
     V.lib()
     wl = workload(args.workload)
+    prec = PRECISION.get(args.workload, 0)
     wl, vis, cal, pulses = synth.gen_evn_torch(seed=2 + rank, device="cuda", wl=wl)
     vis = vis.contiguous()
     stream = torch.cuda.current_stream()
@@ -255,7 +313,7 @@ def run_volks(args):
     units = int(sum(max(int(v), 0) for v in nvalid)) * wl.n_bl  # dedispersed APs x (b, d)
 
     def step(x):
-        s = V.Search(wl, x, cal, stream=sptr)
+        s = V.Search(wl, x, cal, stream=sptr, precision=prec)
         c = s.candidates()          # waits for the device, runs the host match
         t = s.timing()
         s.close()
@@ -326,11 +384,32 @@ def run_volks(args):
                    "sample": f"1 baseline x {len(dms)} DM trials x {n_ap} APs (10 s) of this "
                              f"workload, FP64 numpy, {n} trials in {dt:.1f} s"}
         srt = sorted(step_ms)
+        basis = (f"FP32 FMA: {SM_COUNT} SMs x {FP32_LANES} lanes x 2 x {mhz:.0f} MHz "
+                 "(max SM clock, MEASURED_PEAKS.json)")
+        if prec == 0:
+            roofline = {"bound": "alu", "kernel": "search_kernel<16,4>",
+                        "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                        "frac": achieved / peak, "traffic": traffic, "peak_basis": basis,
+                        "kernel_ms": ms_k, "algorithmic_flops": flops}
+        else:
+            alu = cuda_core_flops_mma(wl, nvalid)
+            mma = mma_flops(wl, nvalid, prec)
+            tpeak = float(peaks.get("bf16_tflops", 1817.4)) * (2.0 if prec == 3 else 1.0)
+            roofline = {"bound": "alu", "kernel": f"search_mma_kernel<16,1,{prec}>",
+                        "achieved": alu / (ms_k / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                        "frac": alu / (ms_k / 1e3) / 1e12 / peak, "traffic": traffic,
+                        "peak_basis": basis, "kernel_ms": ms_k, "algorithmic_flops": alu,
+                        "fft_form_flops": flops, "fft_form_tflops": achieved,
+                        "tensor": {"achieved": mma / (ms_k / 1e3) / 1e12, "peak": tpeak,
+                                   "unit": "TFLOP/s", "frac": mma / (ms_k / 1e3) / 1e12 / tpeak,
+                                   "executed_mma_flops": mma,
+                                   "peak_basis": "measured bf16 burst (MEASURED_PEAKS.json)"
+                                                 + (" x 2 (fp8/bf16 nominal ratio)" if prec == 3 else "")}}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t_max_s * 1e3 / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[prec],
             "data": "synthetic: complex64 N(0,1) noise + 20 dispersed pulses + station RFI",
             "config": {"workload": args.workload, "n_bl": wl.n_bl, "n_ap": wl.n_ap,
                        "n_if": wl.n_if, "n_chan": wl.n_chan, "n_dm": wl.n_dm,
@@ -340,12 +419,7 @@ def run_volks(args):
                        "input_bytes": wl.n_bl * wl.n_ap * wl.n_f * 8,
                        "l2": "inputs larger than L2 (3.6 GB per step)",
                        "step_ms_p50": srt[len(srt) // 2], "step_ms_p99": srt[-1]},
-            "roofline": {"bound": "alu", "kernel": "search_kernel<16,4>",
-                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "peak_basis": f"FP32 FMA: {SM_COUNT} SMs x {FP32_LANES} lanes x 2 x "
-                                       f"{mhz:.0f} MHz (max SM clock, MEASURED_PEAKS.json)",
-                         "kernel_ms": ms_k, "algorithmic_flops": flops},
+            "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": wl.n_bl * wl.n_ap * wl.n_f * 8,

@@ -33,15 +33,27 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// try_wait: like test_wait, but a thread whose phase is not complete may be
+// suspended (for a hardware-defined time) until it completes.
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
 // Wait for the phase with the given parity to complete, giving up after
 // `limit` clock cycles.  Returns false on timeout.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit) {
-  if (mbar_test(bar, parity)) return true;
+  if (mbar_try(bar, parity)) return true;
   const long long t0 = clock64();
   for (;;) {
-    if (mbar_test(bar, parity)) return true;
+    if (mbar_try(bar, parity)) return true;
     if (clock64() - t0 > limit) return false;
-    __nanosleep(20);
   }
 }
 
@@ -71,17 +83,28 @@ __device__ __forceinline__ void fence_after_sync() {
 }
 
 // ---- operand descriptors ---------------------------------------------------
-// Shared-memory matrix descriptor, no swizzle (canonical "interleaved"
-// K-major layout): 8-row x 16-byte core matrices stored as 128 contiguous
-// bytes; lbo = byte distance between core matrices adjacent along K, sbo =
-// byte distance between 8-row groups along M (or N).
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+// Shared-memory matrix descriptor of a K-major operand in one of the
+// swizzled canonical layouts: rows of `row_bytes` (128, 64 or 32) bytes,
+// the 16-byte chunk index of each row XOR-ed with address bits 7.. (the
+// row's position within its 8-row group, scaled to the swizzle width), so
+// the tensor core reads one K chunk of 8 consecutive rows from 8 different
+// bank groups.  sbo = 8 * row_bytes (8-row group stride).  The operand
+// base must be aligned to 1024 bytes; K offsets within a row are added to
+// the start address.
+__device__ __forceinline__ uint64_t sdesc_sw(uint32_t saddr, uint32_t row_bytes) {
+  const uint32_t mode = row_bytes == 128 ? 2u : row_bytes == 64 ? 4u : 6u;  // 128B / 64B / 32B swizzle
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1 << 46;  // descriptor version of the sm_100 family
-  return d;                // base offset 0, relative LBO, swizzle none
+  d |= (uint64_t)1 << 16;                                    // leading byte offset (unused)
+  d |= (uint64_t)(((8u * row_bytes) >> 4) & 0x3FFFu) << 32;  // stride byte offset
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)mode << 61;
+  return d;
+}
+// Byte offset of K byte `kb` of row `r` in that swizzled layout.
+__host__ __device__ constexpr uint32_t sw_offset(uint32_t r, uint32_t kb, uint32_t row_bytes) {
+  const uint32_t f = row_bytes == 128 ? (r & 7u) : row_bytes == 64 ? ((r >> 1) & 3u) : ((r >> 2) & 1u);
+  return r * row_bytes + ((((kb >> 4) ^ f) & (row_bytes / 16 - 1)) << 4) + (kb & 15u);
 }
 
 // Instruction descriptor of a dense kind::f16 MMA: D in FP32, A and B both
@@ -97,6 +120,26 @@ __host__ __device__ constexpr uint32_t idesc_f16(int n, bool bf16) {
 // K-major, M = 128.
 __host__ __device__ constexpr uint32_t idesc_e4m3(int n) {
   return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T with a compile-time accumulate flag.
+template <bool ACC>
+__device__ __forceinline__ void mma_f16_c(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "n"((int)ACC)
+      : "memory");
+}
+template <bool ACC>
+__device__ __forceinline__ void mma_f8_c(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "n"((int)ACC)
+      : "memory");
 }
 
 // D[tmem] (+)= A[smem] * B[smem]^T, issued by one thread.

@@ -748,9 +748,9 @@ int volks_check_rate_gemm(const void* y, int32_t win, int32_t precision, int32_t
   if (!y || !out) return fail(VOLKS_EINVAL, "NULL argument");
   if (flags & ~VOLKS_CHECK_SKIP_MMA) return fail(VOLKS_EINVAL, "unknown flags");
   int l = -1;
-  for (int i = 2; i <= 5; ++i)
+  for (int i = 1; i <= 5; ++i)
     if (win == (1 << i)) l = i;
-  if (l < 0) return fail(VOLKS_EINVAL, "win = %d: 4, 8, 16 or 32 only", win);
+  if (l < 0) return fail(VOLKS_EINVAL, "win = %d: 2, 4, 8, 16 or 32 only", win);
   if (!(precision == VOLKS_BF16 || precision == VOLKS_FP16 || precision == VOLKS_FP8))
     return fail(VOLKS_EINVAL, "precision %d has no tensor-core form", precision);
   const int M = 128;  // W_R^x = W_128^{x 128 / R} for every R = 4 win <= 128

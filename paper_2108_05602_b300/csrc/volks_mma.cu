@@ -14,9 +14,9 @@
 //           type (rows = delay cells, K = 32 APs x (re, im)); per window w,
 //           B = the real embedding of the R = 4w point rate DFT of each
 //           segment, so D[c][2q + {0,1}] = (Re, Im) Z_w[s, q, c]
-//           (Sec. 2.2 2-D search; Sec. 2.4.2 step 6 window combine).  Two
-//           256-column TMEM buffers: the epilogue of one (M-block, window)
-//           job overlaps the MMAs of the next.
+//           (Sec. 2.2 2-D search; Sec. 2.4.2 step 6 window combine).  Warp
+//           0 issues the MMAs; two 256-column TMEM buffers let the other
+//           warps drain one (M-block, window) job while the next one runs.
 //   coarse  epilogue: per (segment, delay cell) the largest coarse |Z|^2
 //           over the segment's rate cells; a warp per segment keeps the
 //           8 delay cells with the largest coarse values (ties: lower cell).
@@ -49,23 +49,24 @@ namespace {
 constexpr int kMRows = 128;          // MMA M: delay cells per M-block
 constexpr int kJobCols = 256;        // TMEM columns of one (M-block, window) job
 constexpr int kTmemCols = 512;       // two job buffers
-constexpr int kGemmSegs = 15;        // segments of windows 4, 8, 16, 32 in a tile
-constexpr int kTopK = 8;             // delay cells refined per segment
+constexpr uint32_t kGemmMask = 0x3cu;  // windows on the tensor cores: 4, 8, 16, 32 (log2 2..5)
+constexpr int kGemmSegs = 15;        // their segments in a tile
+constexpr int kTopK = 8;             // most delay cells refined per segment and unit
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
 template <int PREC>
 struct Op {
   static constexpr int EB = PREC == VOLKS_FP8 ? 1 : 2;      // bytes per element
-  static constexpr uint32_t SBO_A = 512u * EB;              // 8-row group of A
-  static constexpr uint32_t A_BYTES = 16u * SBO_A;          // 128 rows x 64 K
-  // per window l = 2..5: segments per MMA, rows (MMA N), K bytes per row
+  static constexpr uint32_t A_ROW = 64u * EB;               // K bytes of an A row (32 APs x re, im)
+  static constexpr uint32_t A_BYTES = 128u * A_ROW;         // 128 rows
+  // per window l = 1..5: segments per MMA, rows (MMA N), K bytes per row
   static constexpr int seg_per_mma(int l) { return (2 << l) * EB >= 32 ? 1 : 32 / ((2 << l) * EB); }
   static constexpr int b_rows(int l) { return (8 << l) * seg_per_mma(l); }
   static constexpr int b_row_bytes(int l) { return (2 << l) * EB >= 32 ? (2 << l) * EB : 32; }
   static constexpr int b_bytes(int l) { return b_rows(l) * b_row_bytes(l); }
   static constexpr int b_off(int l) {
     int o = 0;
-    for (int i = 2; i < l; ++i) o += b_bytes(i);
+    for (int i = 1; i < l; ++i) o += b_bytes(i);
     return o;
   }
   static constexpr int B_BYTES = b_off(6);
@@ -79,9 +80,11 @@ struct MmaSmem {
   static constexpr size_t S_BYTES = (size_t)32 * (N + 1) * sizeof(float2);
   static constexpr size_t OFF_A = (S_BYTES + 1023) & ~(size_t)1023;
   static constexpr size_t OFF_B = OFF_A + 2 * Op<PREC>::A_BYTES;
-  static constexpr size_t OFF_COL = OFF_B + Op<PREC>::B_BYTES;                // u32 [15][128]
-  static constexpr size_t OFF_TOP = OFF_COL + (size_t)kGemmSegs * kMRows * 4;  // uint2 [15][8]
-  static constexpr size_t OFF_BEST = OFF_TOP + (size_t)kGemmSegs * kTopK * 8;  // u64 [63]
+  static constexpr size_t OFF_COL = OFF_B + Op<PREC>::B_BYTES;                 // u32 [15][128]
+  static constexpr size_t OFF_CAND = OFF_COL + (size_t)kGemmSegs * kMRows * 4;  // uint2 [31][8]
+  static constexpr size_t OFF_CCOUNT = OFF_CAND + (size_t)kGemmSegs * kTopK * 8;  // int [31]
+  static constexpr size_t OFF_RUNMAX = OFF_CCOUNT + 128;                         // u32 [31]
+  static constexpr size_t OFF_BEST = OFF_RUNMAX + 128;                           // u64 [63]
   static constexpr size_t USED = OFF_BEST + (size_t)kMaxSegPerTile * 8;
   // more than half an SM's shared memory: one CTA per SM, so the 512-column
   // TMEM allocation never waits on another CTA
@@ -103,8 +106,8 @@ __device__ __forceinline__ uint32_t e4m3x2(float a, float b) {
   return r;
 }
 
-// Rate-DFT operand B of window 2^l (rows n = MMA N, K-major, interleaved
-// layout), from the FP32 twiddle table W_M^i: row 2q of a segment block
+// Rate-DFT operand B of window 2^l (rows n = MMA N, K-major, swizzled
+// layout of b_row_bytes(l)), from the FP32 twiddle table W_M^i: row 2q of a segment block
 // holds (cos, sin) and row 2q + 1 (-sin, cos) of 2 pi q u / R against
 // (Re, Im) of AP u, so that D = A B^T gives (Re, Im) of
 // Z_q = sum_u Y_u exp(-2 pi i q u / R), R = 4w.  Segments sharing one MMA
@@ -114,10 +117,10 @@ __device__ void build_rate_dft(uint8_t* B, const float2* __restrict__ tw_m, int 
   using O = Op<PREC>;
   constexpr int EB = O::EB;
 #pragma unroll 1
-  for (int l = 2; l <= 5; ++l) {
+  for (int l = 1; l <= 5; ++l) {
     const int w = 1 << l, R = 4 * w;
     const int rows = O::b_rows(l), kel = O::b_row_bytes(l) / EB;
-    const uint32_t sbo = 8u * O::b_row_bytes(l);
+    const uint32_t rb = (uint32_t)O::b_row_bytes(l);
     uint8_t* base = B + O::b_off(l);
 #pragma unroll 1
     for (int i = tid; i < rows * kel; i += nt) {
@@ -129,8 +132,7 @@ __device__ void build_rate_dft(uint8_t* B, const float2* __restrict__ tw_m, int 
         const float2 t = __ldg(tw_m + ((q * u) % R) * (M / R));  // (cos, -sin)
         v = comp == 0 ? (part == 0 ? t.x : -t.y) : (part == 0 ? t.y : t.x);
       }
-      const uint32_t off = (uint32_t)(n >> 3) * sbo + (uint32_t)((k * EB) >> 4) * 128u +
-                           (uint32_t)(n & 7) * 16u + (uint32_t)((k * EB) & 15);
+      const uint32_t off = tc::sw_offset((uint32_t)n, (uint32_t)(k * EB), rb);
       if constexpr (PREC == VOLKS_FP8) {
         base[off] = (uint8_t)(e4m3x2(v, 0.f) & 0xffu);
       } else if constexpr (PREC == VOLKS_BF16) {
@@ -168,39 +170,107 @@ __device__ __forceinline__ void pack_a(const float2* __restrict__ S, uint8_t* A,
         wv[j] = pack2(v.x * scale, v.y * scale, std::integral_constant<int, PREC>{});
       }
     }
-    const uint32_t off = (uint32_t)(row >> 3) * O::SBO_A + (uint32_t)ch * 128u + (uint32_t)(row & 7) * 16u;
+    const uint32_t off = tc::sw_offset((uint32_t)row, (uint32_t)ch * 16u, O::A_ROW);
     *reinterpret_cast<uint4*>(A + off) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
   }
 }
 
-// Issue the MMAs of window 2^l for one M-block into TMEM columns d .. d+255
+// Issue the MMAs of window 2^L for one M-block into TMEM columns d .. d+255
 // (column 8 w s + 2 q + {0,1} = (Re, Im) of rate cell q of segment s).
+// ad / bd: descriptors of the A block and of the window's B at K byte 0;
+// every other operand offset is a compile-time constant added to the
+// descriptors' start-address field (bytes >> 4), so the issuing thread
+// does almost no scalar work between MMAs.
+template <int PREC, int L>
+__device__ __forceinline__ void issue_window_t(uint64_t ad, uint64_t bd, uint32_t d) {
+  using O = Op<PREC>;
+  constexpr int EB = O::EB;
+  constexpr int w = 1 << L;
+  constexpr int seg_kb = 2 * w * EB;  // K bytes of one segment; one MMA consumes 32
+  if constexpr (seg_kb >= 32) {
+    constexpr int nseg = 32 / w, n = 8 * w, ks = seg_kb / 32;
+    constexpr uint32_t idesc = PREC == VOLKS_FP8 ? tc::idesc_e4m3(n) : tc::idesc_f16(n, PREC == VOLKS_BF16);
+    static_for<0, nseg>([&](auto ss) {
+      constexpr int s = decltype(ss)::value;
+      static_for<0, ks>([&](auto kk) {
+        constexpr int k = decltype(kk)::value;
+        const uint64_t a = ad + (uint64_t)((seg_kb * s + 32 * k) >> 4);
+        const uint64_t b = bd + (uint64_t)((32 * k) >> 4);
+        if constexpr (PREC == VOLKS_FP8) tc::mma_f8_c<(k > 0)>(d + (uint32_t)(n * s), a, b, idesc);
+        else tc::mma_f16_c<(k > 0)>(d + (uint32_t)(n * s), a, b, idesc);
+      });
+    });
+  } else {
+    constexpr int g = 32 / seg_kb, n = 8 * w * g, ngrp = (32 / w) / g;
+    constexpr uint32_t idesc = PREC == VOLKS_FP8 ? tc::idesc_e4m3(n) : tc::idesc_f16(n, PREC == VOLKS_BF16);
+    static_for<0, ngrp>([&](auto pp) {
+      constexpr int p = decltype(pp)::value;
+      const uint64_t a = ad + (uint64_t)((32 * p) >> 4);
+      if constexpr (PREC == VOLKS_FP8) tc::mma_f8_c<false>(d + (uint32_t)(n * p), a, bd, idesc);
+      else tc::mma_f16_c<false>(d + (uint32_t)(n * p), a, bd, idesc);
+    });
+  }
+}
+
+// One MMA of a window's job: K byte offset into the A block, byte offset
+// into the window's B (both multiples of 16), TMEM column, and the
+// instruction descriptor with the accumulate flag in bit 31.
+struct MmaOp {
+  uint16_t a16, b16, dcol;
+  uint16_t _pad;
+  uint32_t idesc_acc;
+};
+constexpr int kMaxOpsPerJob = 4;
+
+// The MMAs of window 2^l (same sequence as issue_window_t) into ops[].
 template <int PREC>
-__device__ __forceinline__ void issue_window(int l, uint32_t a_base, uint32_t b_base, uint32_t d) {
+__device__ int job_ops(int l, MmaOp* ops) {
   using O = Op<PREC>;
   constexpr int EB = O::EB;
   const int w = 1 << l;
-  const int seg_kb = 2 * w * EB;  // K bytes of one segment; one MMA consumes 32
-  const uint32_t sbo_b = 8u * (uint32_t)O::b_row_bytes(l);
+  const int seg_kb = 2 * w * EB;
+  int n_ops = 0;
   if (seg_kb >= 32) {
     const int nseg = 32 / w, n = 8 * w, ks = seg_kb / 32;
     const uint32_t idesc = PREC == VOLKS_FP8 ? tc::idesc_e4m3(n) : tc::idesc_f16(n, PREC == VOLKS_BF16);
     for (int s = 0; s < nseg; ++s)
-      for (int k = 0; k < ks; ++k) {
-        const uint64_t ad = tc::sdesc(a_base + (uint32_t)(16 * w * EB * s + 256 * k), 128u, O::SBO_A);
-        const uint64_t bd = tc::sdesc(b_base + (uint32_t)(256 * k), 128u, sbo_b);
-        if constexpr (PREC == VOLKS_FP8) tc::mma_f8(d + (uint32_t)(n * s), ad, bd, idesc, k > 0);
-        else tc::mma_f16(d + (uint32_t)(n * s), ad, bd, idesc, k > 0);
-      }
+      for (int k = 0; k < ks; ++k)
+        ops[n_ops++] = MmaOp{(uint16_t)((seg_kb * s + 32 * k) >> 4), (uint16_t)((32 * k) >> 4),
+                             (uint16_t)(n * s), 0, idesc | (k > 0 ? 0x80000000u : 0u)};
   } else {
     const int g = 32 / seg_kb, n = 8 * w * g, ngrp = (32 / w) / g;
     const uint32_t idesc = PREC == VOLKS_FP8 ? tc::idesc_e4m3(n) : tc::idesc_f16(n, PREC == VOLKS_BF16);
-    for (int p = 0; p < ngrp; ++p) {
-      const uint64_t ad = tc::sdesc(a_base + (uint32_t)(256 * p), 128u, O::SBO_A);
-      const uint64_t bd = tc::sdesc(b_base, 128u, sbo_b);
-      if constexpr (PREC == VOLKS_FP8) tc::mma_f8(d + (uint32_t)(n * p), ad, bd, idesc, false);
-      else tc::mma_f16(d + (uint32_t)(n * p), ad, bd, idesc, false);
-    }
+    for (int p = 0; p < ngrp; ++p)
+      ops[n_ops++] = MmaOp{(uint16_t)((32 * p) >> 4), 0, (uint16_t)(n * p), 0, idesc};
+  }
+  return n_ops;
+}
+
+// Issue one job from its op table: a compact loop, so the issuing warp's
+// code stays small and resident in the instruction cache.
+template <int PREC>
+__device__ __forceinline__ void issue_ops(const MmaOp* ops, int n_ops, uint64_t ad, uint64_t bd, uint32_t d) {
+#pragma unroll 1
+  for (int i = 0; i < n_ops; ++i) {
+    const MmaOp o = ops[i];
+    const uint32_t idesc = o.idesc_acc & 0x7fffffffu;
+    const bool acc = (o.idesc_acc >> 31) != 0;
+    if constexpr (PREC == VOLKS_FP8) tc::mma_f8(d + o.dcol, ad + o.a16, bd + o.b16, idesc, acc);
+    else tc::mma_f16(d + o.dcol, ad + o.a16, bd + o.b16, idesc, acc);
+  }
+}
+
+template <int PREC>
+__device__ __forceinline__ void issue_window(int l, uint32_t a_base, uint32_t b_base, uint32_t d) {
+  using O = Op<PREC>;
+  const uint64_t ad = tc::sdesc_sw(a_base, O::A_ROW);
+  const uint64_t bd = tc::sdesc_sw(b_base, (uint32_t)O::b_row_bytes(l));
+  switch (l) {
+    case 1: issue_window_t<PREC, 1>(ad, bd, d); break;
+    case 2: issue_window_t<PREC, 2>(ad, bd, d); break;
+    case 3: issue_window_t<PREC, 3>(ad, bd, d); break;
+    case 4: issue_window_t<PREC, 4>(ad, bd, d); break;
+    default: issue_window_t<PREC, 5>(ad, bd, d); break;
   }
 }
 
@@ -238,24 +308,195 @@ __device__ __forceinline__ unsigned long long warp_key(float p, uint32_t lin) {
 
 struct MmaCtx {
   uint32_t tmem;        // TMEM base address (512 columns)
-  uint32_t phase[2];    // parity of the next completion of each job buffer
+  uint32_t f_par[2];    // consumers: parity of the next completion of each job buffer
+  uint32_t n_use[2];    // producer: jobs issued into each buffer so far
+  uint32_t a_par[2];    // producer: parity of the next pack of each A buffer
 };
 
-// One unit on the tensor-core path.  Returns false if a wait for the MMAs
-// timed out (the error flag is set; the caller stops).
+struct JobTable {
+  MmaOp ops[6][kMaxOpsPerJob];  // by window log2 (1..5)
+  int n_ops[6];
+};
+
+struct MmaBars {
+  uint64_t full[2];     // MMAs of the job in TMEM buffer i completed (tcgen05.commit)
+  uint64_t empty[2];    // every consumer warp has drained TMEM buffer i
+  uint64_t afull[2];    // every consumer warp has packed its share of A buffer i
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
+}
+// Barrier 1 over the consumer warps only (the producer warp keeps issuing).
+template <int NTHREADS>
+__device__ __forceinline__ void consumer_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(NTHREADS) : "memory");
+}
+
+// Candidate delay cells of a segment (per CTA unit): the cells whose coarse
+// power is at least kKeep[PREC] times the segment's coarse maximum, at most
+// kTopK of them (the largest; ties to the lower cell).  kKeep = 1 - delta,
+// delta ~4x the coarse relative error of |Z|^2 at a peak for the operand
+// type, so the FP32 peak's cell is retained unless more than kTopK cells
+// lie within delta of the coarse maximum.
+template <int PREC>
+struct Keep {
+  static constexpr float value = PREC == VOLKS_FP8 ? 1.0f - 1.0f / 4 : PREC == VOLKS_FP16 ? 1.0f - 1.0f / 64 : 1.0f - 1.0f / 16;
+};
+
+// Merge the coarse column maxima of one 128-cell block (v[i] at cell
+// c[i], four per lane) into segment sg's candidate list (one warp).
+template <int PREC>
+__device__ __forceinline__ void merge_block(uint32_t (&v)[4], uint32_t (&c)[4], uint2* cand, int* ccount,
+                                            uint32_t* runmax, int sg, int lane) {
+  const int on = ccount[sg];
+  uint32_t ov = 0u, oc = 0xffffffffu;
+  if (lane < on) {
+    const uint2 t = cand[sg * kTopK + lane];
+    ov = t.x;
+    oc = t.y;
+  }
+  uint32_t bm = max(max(v[0], v[1]), max(v[2], v[3]));
+  bm = __reduce_max_sync(0xffffffffu, bm);
+  const uint32_t mx = max(runmax[sg], bm);
+  const uint32_t thr = __float_as_uint(__uint_as_float(mx) * Keep<PREC>::value);
+  const bool ko = lane < on && ov >= thr;
+  bool kn[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) kn[i] = v[i] >= thr;
+  const uint32_t bo = __ballot_sync(0xffffffffu, ko);
+  uint32_t bn[4];
+  int total = __popc(bo);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    bn[i] = __ballot_sync(0xffffffffu, kn[i]);
+    total += __popc(bn[i]);
+  }
+  __syncwarp();
+  if (total <= kTopK) {
+    const uint32_t lt = (1u << lane) - 1u;
+    int base = 0;
+    if (ko) cand[sg * kTopK + base + __popc(bo & lt)] = make_uint2(ov, oc);
+    base += __popc(bo);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (kn[i]) cand[sg * kTopK + base + __popc(bn[i] & lt)] = make_uint2(v[i], c[i]);
+      base += __popc(bn[i]);
+    }
+  } else {
+    // the kTopK largest of the retained cells (value, then lower cell)
+    if (!ko) {
+      ov = 0u;
+      oc = 0xffffffffu;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (!kn[i]) {
+        v[i] = 0u;
+        c[i] = 0xffffffffu;
+      }
+    uint2 out = make_uint2(0u, 0xffffffffu);
+#pragma unroll 1
+    for (int rr = 0; rr < kTopK; ++rr) {
+      uint32_t bv = ov, bc = oc;
+      int bi = 4;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (v[i] > bv || (v[i] == bv && c[i] < bc)) {
+          bv = v[i];
+          bc = c[i];
+          bi = i;
+        }
+      const uint32_t wv = __reduce_max_sync(0xffffffffu, bv);
+      const uint32_t wc = __reduce_min_sync(0xffffffffu, bv == wv ? bc : 0xffffffffu);
+      if (lane == rr) out = make_uint2(wv, wc);
+      if (bv == wv && bc == wc) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (bi == i) {
+            v[i] = 0u;
+            c[i] = 0xffffffffu;
+          }
+        if (bi == 4) {
+          ov = 0u;
+          oc = 0xffffffffu;
+        }
+      }
+    }
+    if (lane < kTopK) cand[sg * kTopK + lane] = out;
+    total = kTopK;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    ccount[sg] = total;
+    runmax[sg] = mx;
+  }
+  __syncwarp();
+}
+
+// Drain this warp's 32-column chunks [ch0, ch1) of one job (window 2^L) from
+// TMEM: load, hand the buffer back to the producer (mbarrier `empty`),
+// then fold coarse |Z|^2 into the per-segment column maxima cm[s * 128]
+// (segment s of the window = columns 8 w s .. 8 w s + 8 w - 1).
+template <int L>
+__device__ __forceinline__ void drain_job(uint32_t tb, uint32_t* cm, int ch0, int ch1, uint64_t* empty,
+                                          int lane) {
+  constexpr int SEGC = 8 << L;  // columns per segment
+  auto fold = [&](const uint32_t (&v)[32], int ch) {
+    if constexpr (SEGC == 16) {
+      float m[2] = {0.f, 0.f};
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int i = 16 * h; i < 16 * h + 16; i += 4) {
+          const float a0 = __uint_as_float(v[i]), a1 = __uint_as_float(v[i + 1]);
+          const float a2 = __uint_as_float(v[i + 2]), a3 = __uint_as_float(v[i + 3]);
+          m[h] = tc::fmax3(m[h], fmaf(a0, a0, a1 * a1), fmaf(a2, a2, a3 * a3));
+        }
+      atomicMax(cm + (2 * ch) * kMRows, __float_as_uint(m[0]));
+      atomicMax(cm + (2 * ch + 1) * kMRows, __float_as_uint(m[1]));
+    } else {
+      float m = 0.f;
+#pragma unroll
+      for (int i = 0; i < 32; i += 4) {
+        const float a0 = __uint_as_float(v[i]), a1 = __uint_as_float(v[i + 1]);
+        const float a2 = __uint_as_float(v[i + 2]), a3 = __uint_as_float(v[i + 3]);
+        m = tc::fmax3(m, fmaf(a0, a0, a1 * a1), fmaf(a2, a2, a3 * a3));
+      }
+      atomicMax(cm + ((ch * 32) / SEGC) * kMRows, __float_as_uint(m));
+    }
+  };
+#pragma unroll 1
+  for (int ch = ch0; ch < ch1; ++ch) {
+    uint32_t v[32];
+    tc::tmem_ld32(tb + (uint32_t)ch * 32u, v);
+    tc::tmem_wait_ld();
+    if (ch + 1 == ch1) {
+      // accumulators are in registers: release the TMEM buffer
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(empty);
+    }
+    fold(v, ch);
+  }
+}
+
+// One unit on the tensor-core path.  Returns false if a bounded wait gave
+// up (the error flag is set; the caller stops).
 template <int N1, int FOLD, int PREC>
-__device__ __forceinline__ bool mma_tile(const UnitState& us, uint8_t* smem, MmaCtx& cx, uint64_t* bar,
-                                         float* s_amax, unsigned int* err) {
+__device__ __forceinline__ bool mma_tile(const UnitState& us, uint8_t* smem, MmaCtx& cx, MmaBars& bars,
+                                         const JobTable& jt, float* s_amax, unsigned int* err) {
   using O = Op<PREC>;
   using L = MmaSmem<N1, PREC>;
   constexpr int N = 32 * N1, LD = N + 1, NT = N, NW = N1, NMB = N / kMRows;
-  constexpr int G = NW / 4;             // warps sharing one TMEM lane quarter
-  constexpr int CPT = 8 / G;            // 32-column chunks per thread per job
+  constexpr int NC = NW - 1;            // consumer warps (warp 0 issues the MMAs)
   float2* S = reinterpret_cast<float2*>(smem);
   uint8_t* A = smem + L::OFF_A;
   uint8_t* Bm = smem + L::OFF_B;
   uint32_t* colmax = reinterpret_cast<uint32_t*>(smem + L::OFF_COL);
-  uint2* top = reinterpret_cast<uint2*>(smem + L::OFF_TOP);
+  uint2* cand = reinterpret_cast<uint2*>(smem + L::OFF_CAND);
+  int* ccount = reinterpret_cast<int*>(smem + L::OFF_CCOUNT);
+  uint32_t* runmax = reinterpret_cast<uint32_t*>(smem + L::OFF_RUNMAX);
   unsigned long long* best = reinterpret_cast<unsigned long long*>(smem + L::OFF_BEST);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
@@ -273,18 +514,22 @@ __device__ __forceinline__ bool mma_tile(const UnitState& us, uint8_t* smem, Mma
     return o;
   };
   auto seg_valid = [&](int l, int s) { return ((t0 >> l) + s + 1) << l <= nv; };
-  // GEMM windows (4..32) present; sigma numbers their segments in
+  // GEMM windows (2..32) present; sigma numbers their segments in
   // ascending window order
-  const uint32_t gmask = (uint32_t)win_mask & 0x3cu;
+  const uint32_t gmask = (uint32_t)win_mask & kGemmMask;
   const int nG = __popc(gmask);
-  auto gwin = [&](int i) { return __fns(gmask, 0, i + 1); };  // log2 of the i-th GEMM window
-  auto sig_base = [&](int l) {
-    int o = 0;
-    for (int i = 2; i < l; ++i)
-      if (gmask & (1u << i)) o += kTile >> i;
-    return o;
-  };
-  const int nsig = sig_base(6);
+  // gl: log2 of the i-th GEMM window in bits 3i..3i+2; sb: first sigma of
+  // window 2^l in bits 5l..5l+4
+  uint32_t gl = 0u, sb = 0u;
+  int nsig = 0;
+  for (int l = 1, i = 0; l <= 5; ++l)
+    if (gmask & (1u << l)) {
+      gl |= (uint32_t)l << (3 * i++);
+      sb |= (uint32_t)nsig << (5 * l);
+      nsig += kTile >> l;
+    }
+  auto gwin = [&](int i) { return (int)((gl >> (3 * i)) & 7u); };
+  auto sig_base = [&](int l) { return (int)((sb >> (5 * l)) & 31u); };
   const int njobs = NMB * nG;
 
   float scale = 1.f;
@@ -309,186 +554,176 @@ __device__ __forceinline__ bool mma_tile(const UnitState& us, uint8_t* smem, Mma
     pack_a<LD, PREC>(S, A, 0, scale, tid, NT);
     if (NMB > 1) pack_a<LD, PREC>(S, A + O::A_BYTES, 1, scale, tid, NT);
     for (int i = tid; i < nsig * kMRows; i += NT) colmax[i] = 0u;
-    for (int i = tid; i < nsig * kTopK; i += NT) top[i] = make_uint2(0u, 0xffffffffu);
+    for (int i = tid; i < nsig; i += NT) {
+      ccount[i] = 0;
+      runmax[i] = 0u;
+    }
     tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
-    tc::fence_after_sync();
-    if (tid == 0) {
-      for (int j = 0; j < 2 && j < njobs; ++j) {
-        const int b = j / nG, l = gwin(j % nG);
-        issue_window<PREC>(l, tc::smem_u32(A + (b & 1) * O::A_BYTES), tc::smem_u32(Bm + O::b_off(l)),
-                           cx.tmem + (uint32_t)(j & 1) * kJobCols);
-        tc::mma_commit(&bar[j & 1]);
-      }
-    }
   }
 
-  // ---- exact windows on the CUDA cores (overlap the first MMAs) ----
-  if (win_mask & 1) {
-    for (int s = warp; s < kTile; s += NW) {
-      if (!seg_valid(0, s)) continue;
-      float bp = -1.f;
-      int bc = 0;
+  bool ok = true;
+  if (warp == 0) {
+    // ---- producer: issue every job as its TMEM buffer and A block are ready ----
+    if (lane == 0) {
+      int j = 0;
+      for (int b = 0; ok && nG > 0 && b < NMB; ++b) {
+        if (b >= 2) {
+          ok = tc::mbar_wait_bounded(&bars.afull[b & 1], cx.a_par[b & 1], kWaitCycles);
+          cx.a_par[b & 1] ^= 1u;
+        }
+        const uint32_t a_addr = tc::smem_u32(A + (b & 1) * O::A_BYTES);
+        for (int gi = 0; ok && gi < nG; ++gi, ++j) {
+          const int buf = j & 1, l = gwin(gi);
+          if (cx.n_use[buf] > 0)
+            ok = tc::mbar_wait_bounded(&bars.empty[buf], (cx.n_use[buf] - 1u) & 1u, kWaitCycles);
+          if (!ok) break;
+          tc::fence_after_sync();
+          issue_ops<PREC>(jt.ops[l], jt.n_ops[l], tc::sdesc_sw(a_addr, O::A_ROW),
+                          tc::sdesc_sw(tc::smem_u32(Bm + O::b_off(l)), (uint32_t)O::b_row_bytes(l)),
+                          cx.tmem + (uint32_t)buf * kJobCols);
+          tc::mma_commit(&bars.full[buf]);
+          ++cx.n_use[buf];
+        }
+      }
+    }
+    __syncwarp();
+  } else {
+    // ---- consumers: exact windows while the first MMAs run ----
+    if (win_mask & 1) {
+      for (int s = warp - 1; s < kTile; s += NC) {
+        if (!seg_valid(0, s)) continue;
+        float bp = -1.f;
+        int bc = 0;
 #pragma unroll 4
-      for (int j = 0; j < N1; ++j) {
-        const int c = lane + 32 * j;
-        const float p = cabs2(S[s * LD + c]);
-        if (p > bp) {
-          bp = p;
-          bc = c;
+        for (int j = 0; j < N1; ++j) {
+          const int c = lane + 32 * j;
+          const float p = cabs2(S[s * LD + c]);
+          if (p > bp) {
+            bp = p;
+            bc = c;
+          }
         }
+        const unsigned long long key = warp_key(bp, (uint32_t)(bc * P + r));
+        if (lane == 0) best[slot_base(0) + s] = key;
       }
-      const unsigned long long key = warp_key(bp, (uint32_t)(bc * P + r));
-      if (lane == 0) best[slot_base(0) + s] = key;
     }
-  }
-  if (win_mask & 2) {
-    for (int s = warp; s < kTile / 2; s += NW) {
-      if (!seg_valid(1, s)) continue;
-      float bp = -1.f;
-      uint32_t bl = 0xffffffffu;
+    if (win_mask & 2) {
+      for (int s = warp - 1; s < kTile / 2; s += NC) {
+        if (!seg_valid(1, s)) continue;
+        float bp = -1.f;
+        uint32_t bl = 0xffffffffu;
 #pragma unroll 2
-      for (int j = 0; j < N1; ++j) {
-        const int c = lane + 32 * j;
-        float P8[8];
-        rate_cells_w2(S[(2 * s) * LD + c], S[(2 * s + 1) * LD + c], P8);
-        float pv;
-        uint32_t qv;
-        argmax_tree<0, 8>([&](auto qq) { return P8[decltype(qq)::value]; }, pv, qv);
-        const uint32_t lin = qv * M + (uint32_t)(c * P + r);
-        if (pv > bp || (pv == bp && lin < bl)) {
-          bp = pv;
-          bl = lin;
+        for (int j = 0; j < N1; ++j) {
+          const int c = lane + 32 * j;
+          float P8[8];
+          rate_cells_w2(S[(2 * s) * LD + c], S[(2 * s + 1) * LD + c], P8);
+          float pv;
+          uint32_t qv;
+          argmax_tree<0, 8>([&](auto qq) { return P8[decltype(qq)::value]; }, pv, qv);
+          const uint32_t lin = qv * M + (uint32_t)(c * P + r);
+          if (pv > bp || (pv == bp && lin < bl)) {
+            bp = pv;
+            bl = lin;
+          }
+        }
+        const unsigned long long key = warp_key(bp, bl);
+        if (lane == 0) best[slot_base(1) + s] = key;
+      }
+    }
+    // ---- consumers: drain each job's accumulators ----
+    const int q = warp & 3;
+    const int cnt = NW / 4 - (q == 0 ? 1 : 0);           // consumer warps of lane quarter q
+    const int k = (warp >> 2) - (q == 0 ? 1 : 0);
+    const int ch0 = (k * 8) / cnt, ch1 = ((k + 1) * 8) / cnt;  // 32-column chunks of this warp
+    const int row = q * 32 + lane;
+    int j = 0;
+#pragma unroll 1
+    for (int b = 0; b < NMB; ++b) {
+#pragma unroll 1
+      for (int gi = 0; gi < nG; ++gi, ++j) {
+        const int buf = j & 1, l = gwin(gi);
+        const bool last = gi == nG - 1;
+        // after a failed wait the warp keeps walking the loop (no more waits,
+        // no TMEM reads) so that every barrier below is still reached
+        // one lane per warp waits (the others idle at the shuffle)
+        if (ok) {
+          bool w_ok = true;
+          if (lane == 0) w_ok = tc::mbar_wait_bounded(&bars.full[buf], cx.f_par[buf], kWaitCycles);
+          ok = __shfl_sync(0xffffffffu, w_ok, 0);
+        }
+        cx.f_par[buf] ^= 1u;
+        tc::fence_after_sync();
+        if (last && b + 2 < NMB) {
+          // every MMA reading A block b has completed: refill its buffer with block b + 2
+          if (ok) {
+            pack_a<LD, PREC>(S, A + (b & 1) * O::A_BYTES, b + 2, scale, tid - 32, NT - 32);
+            tc::fence_async_smem();
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&bars.afull[b & 1]);
+        }
+        const uint32_t tb = cx.tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * kJobCols;
+        uint32_t* cm = colmax + sig_base(l) * kMRows + row;
+        if (ok) {
+          switch (l) {
+            case 1: drain_job<1>(tb, cm, ch0, ch1, &bars.empty[buf], lane); break;
+            case 2: drain_job<2>(tb, cm, ch0, ch1, &bars.empty[buf], lane); break;
+            case 3: drain_job<3>(tb, cm, ch0, ch1, &bars.empty[buf], lane); break;
+            case 4: drain_job<4>(tb, cm, ch0, ch1, &bars.empty[buf], lane); break;
+            default: drain_job<5>(tb, cm, ch0, ch1, &bars.empty[buf], lane); break;
+          }
+        } else {
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&bars.empty[buf]);
+        }
+        if (last) {
+          // M-block b complete: merge its cells into every segment's candidates
+          consumer_sync<NT - 32>();
+          for (int sg = warp - 1; sg < nsig; sg += NC) {
+            uint32_t v[4], c[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              v[i] = colmax[sg * kMRows + lane + 32 * i];
+              c[i] = (uint32_t)(b * kMRows + lane + 32 * i);
+              colmax[sg * kMRows + lane + 32 * i] = 0u;
+            }
+            merge_block<PREC>(v, c, cand, ccount, runmax, sg, lane);
+          }
+          consumer_sync<NT - 32>();
         }
       }
-      const unsigned long long key = warp_key(bp, bl);
-      if (lane == 0) best[slot_base(1) + s] = key;
     }
   }
-
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0) atomicOr(err, 1u);
+    return false;
+  }
   if (nG > 0) {
-    const int quarter = warp & 3, g = warp >> 2;
-    const int row = quarter * 32 + lane;
-#pragma unroll 1
-    for (int j = 0; j < njobs; ++j) {
-      const int buf = j & 1, b = j / nG, l = gwin(j % nG);
-      const bool ok = tc::mbar_wait_bounded(&bar[buf], cx.phase[buf], kWaitCycles);
-      cx.phase[buf] ^= 1u;
-      if (__syncthreads_or(!ok)) {
-        if (tid == 0) atomicOr(err, 1u);
-        return false;
-      }
-      tc::fence_after_sync();
-      // epilogue: coarse |Z|^2, max over each segment's rate cells
-      const uint32_t tb = cx.tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)buf * kJobCols;
-#pragma unroll 1
-      for (int ch = g * CPT; ch < (g + 1) * CPT; ch += 2) {
-        uint32_t v0[32], v1[32];
-        tc::tmem_ld32(tb + (uint32_t)ch * 32u, v0);
-        tc::tmem_ld32(tb + (uint32_t)(ch + 1) * 32u, v1);
-        tc::tmem_wait_ld();
-        float m0 = 0.f, m1 = 0.f;
-#pragma unroll
-        for (int i = 0; i < 32; i += 4) {
-          const float a0 = __uint_as_float(v0[i]), a1 = __uint_as_float(v0[i + 1]);
-          const float a2 = __uint_as_float(v0[i + 2]), a3 = __uint_as_float(v0[i + 3]);
-          m0 = tc::fmax3(m0, fmaf(a0, a0, a1 * a1), fmaf(a2, a2, a3 * a3));
-          const float c0 = __uint_as_float(v1[i]), c1 = __uint_as_float(v1[i + 1]);
-          const float c2 = __uint_as_float(v1[i + 2]), c3 = __uint_as_float(v1[i + 3]);
-          m1 = tc::fmax3(m1, fmaf(c0, c0, c1 * c1), fmaf(c2, c2, c3 * c3));
-        }
-        const int s0 = (ch * 32) >> (l + 3), s1 = ((ch + 1) * 32) >> (l + 3);
-        uint32_t* cm = colmax + sig_base(l) * kMRows + row;
-        if (s0 == s1) {
-          atomicMax(cm + s0 * kMRows, __float_as_uint(fmaxf(m0, m1)));
-        } else {
-          atomicMax(cm + s0 * kMRows, __float_as_uint(m0));
-          atomicMax(cm + s1 * kMRows, __float_as_uint(m1));
-        }
-      }
-      tc::fence_before_sync();
-      __syncthreads();
-      if (j % nG == nG - 1) {
-        // M-block b done: merge its 128 delay cells into each segment's top 8
-        for (int sg = warp; sg < nsig; sg += NW) {
-          uint32_t v[4], cidx[4];
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            v[i] = colmax[sg * kMRows + lane + 32 * i];
-            cidx[i] = (uint32_t)(b * kMRows + lane + 32 * i);
-            colmax[sg * kMRows + lane + 32 * i] = 0u;
-          }
-          uint32_t v4 = 0u, c4 = 0xffffffffu;
-          if (lane < kTopK) {
-            const uint2 t = top[sg * kTopK + lane];
-            v4 = t.x;
-            c4 = t.y;
-          }
-          uint2 out = make_uint2(0u, 0xffffffffu);
-#pragma unroll 1
-          for (int rr = 0; rr < kTopK; ++rr) {
-            uint32_t bv = v4, bc = c4;
-            int bi = 4;
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-              if (v[i] > bv || (v[i] == bv && cidx[i] < bc)) {
-                bv = v[i];
-                bc = cidx[i];
-                bi = i;
-              }
-            const uint32_t wv = __reduce_max_sync(0xffffffffu, bv);
-            const uint32_t wc = __reduce_min_sync(0xffffffffu, bv == wv ? bc : 0xffffffffu);
-            if (lane == rr) out = make_uint2(wv, wc);
-            if (bv == wv && bc == wc) {
-#pragma unroll
-              for (int i = 0; i < 4; ++i)
-                if (bi == i) {
-                  v[i] = 0u;
-                  cidx[i] = 0xffffffffu;
-                }
-              if (bi == 4) {
-                v4 = 0u;
-                c4 = 0xffffffffu;
-              }
-            }
-          }
-          if (lane < kTopK) top[sg * kTopK + lane] = out;
-        }
-        if (b + 2 < NMB) {
-          pack_a<LD, PREC>(S, A + (b & 1) * O::A_BYTES, b + 2, scale, tid, NT);
-          tc::fence_async_smem();
-        }
-        __syncthreads();
-      }
-      tc::fence_after_sync();
-      if (tid == 0 && j + 2 < njobs) {
-        const int j2 = j + 2, b2 = j2 / nG, l2 = gwin(j2 % nG);
-        issue_window<PREC>(l2, tc::smem_u32(A + (b2 & 1) * O::A_BYTES), tc::smem_u32(Bm + O::b_off(l2)),
-                           cx.tmem + (uint32_t)buf * kJobCols);
-        tc::mma_commit(&bar[buf]);
-      }
-    }
-    // ---- FP32 refinement of the retained delay cells ----
-    for (int sg = warp; sg < nsig; sg += NW) {
+    // ---- FP32 refinement of the candidate delay cells (all warps) ----
+    // descending sigma: the largest windows (longest refinements) go first
+    for (int sg = nsig - 1 - warp; sg >= 0; sg -= NW) {
       int l = gwin(0);
       for (int i = 1; i < nG; ++i)
         if (sg >= sig_base(gwin(i))) l = gwin(i);
       const int s = sg - sig_base(l);
       if (!seg_valid(l, s)) continue;
-      const uint2 t = top[sg * kTopK + (lane >> 2)];
-      const int c = (int)t.y;
+      int ci = lane >> 2;
+      if (ci >= ccount[sg]) ci = 0;
+      const int c = (int)cand[sg * kTopK + ci].y;
       const int rho = lane & 3;
       float pw;
-      uint32_t q;
+      uint32_t qq;
       const int u0 = s << l;
       switch (l) {
-        case 2: refine_column<4, LD>(S, c, u0, rho, tw_m, (int)M, pw, q); break;
-        case 3: refine_column<8, LD>(S, c, u0, rho, tw_m, (int)M, pw, q); break;
-        case 4: refine_column<16, LD>(S, c, u0, rho, tw_m, (int)M, pw, q); break;
-        default: refine_column<32, LD>(S, c, u0, rho, tw_m, (int)M, pw, q); break;
+        case 1: refine_column<2, LD>(S, c, u0, rho, tw_m, (int)M, pw, qq); break;
+        case 2: refine_column<4, LD>(S, c, u0, rho, tw_m, (int)M, pw, qq); break;
+        case 3: refine_column<8, LD>(S, c, u0, rho, tw_m, (int)M, pw, qq); break;
+        case 4: refine_column<16, LD>(S, c, u0, rho, tw_m, (int)M, pw, qq); break;
+        default: refine_column<32, LD>(S, c, u0, rho, tw_m, (int)M, pw, qq); break;
       }
-      const unsigned long long key = warp_key(pw, q * M + (uint32_t)(c * P + r));
+      const unsigned long long key = warp_key(pw, qq * M + (uint32_t)(c * P + r));
       if (lane == 0) best[slot_base(l) + s] = key;
     }
   }
@@ -520,15 +755,20 @@ __global__ void __launch_bounds__(32 * N1, 1) search_mma_kernel(const __grid_con
   __shared__ UnitState us;
   __shared__ int s_desc;
   __shared__ long long s_unit;
-  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ __align__(8) MmaBars bars;
+  __shared__ __align__(8) JobTable jt;
   __shared__ uint32_t s_tmem;
   __shared__ float s_amax;
   const int tid = threadIdx.x;
   using L = MmaSmem<N1, PREC>;
   build_rate_dft<PREC>(smem + L::OFF_B, p.d[0].tw_m, p.d[0].M, tid, N);
   if (tid == 0) {
-    tc::mbar_init(&bar[0], 1);
-    tc::mbar_init(&bar[1], 1);
+    for (int l = 1; l <= 5; ++l) jt.n_ops[l] = job_ops<PREC>(l, jt.ops[l]);
+    for (int i = 0; i < 2; ++i) {
+      tc::mbar_init(&bars.full[i], 1);
+      tc::mbar_init(&bars.empty[i], N1 - 1);
+      tc::mbar_init(&bars.afull[i], N1 - 1);
+    }
     tc::mbar_init_fence();
   }
   if ((tid >> 5) == 0) {
@@ -541,7 +781,9 @@ __global__ void __launch_bounds__(32 * N1, 1) search_mma_kernel(const __grid_con
   tc::fence_after_sync();
   MmaCtx cx;
   cx.tmem = s_tmem;
-  cx.phase[0] = cx.phase[1] = 0u;
+  cx.f_par[0] = cx.f_par[1] = 0u;
+  cx.n_use[0] = cx.n_use[1] = 0u;
+  cx.a_par[0] = cx.a_par[1] = 0u;
   for (;;) {
     if (tid == 0) {
       const long long u = (long long)atomicAdd(p.counter, 1ULL);
@@ -572,7 +814,7 @@ __global__ void __launch_bounds__(32 * N1, 1) search_mma_kernel(const __grid_con
       us.valid = us.t0 < us.nv;
     }
     __syncthreads();
-    if (us.valid && !mma_tile<N1, FOLD, PREC>(us, smem, cx, bar, &s_amax, p.err)) break;
+    if (us.valid && !mma_tile<N1, FOLD, PREC>(us, smem, cx, bars, jt, &s_amax, p.err)) break;
     __syncthreads();
   }
   tc::fence_before_sync();
@@ -698,7 +940,7 @@ cudaError_t launch_search_mma(Batch& b, SearchVariant v, int precision, int grid
 
 cudaError_t launch_rate_gemm_probe(const float2* y, const float2* tw_m, int M, int l, int precision, int skip_mma,
                                    float* out, unsigned int* err, cudaStream_t s) {
-  if (l < 2 || l > 5) return cudaErrorInvalidValue;
+  if (l < 1 || l > 5) return cudaErrorInvalidValue;
   switch (precision) {
     case VOLKS_BF16: return launch_probe_t<VOLKS_BF16>(y, tw_m, M, l, skip_mma, out, err, s);
     case VOLKS_FP16: return launch_probe_t<VOLKS_FP16>(y, tw_m, M, l, skip_mma, out, err, s);
