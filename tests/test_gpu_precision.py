@@ -292,3 +292,107 @@ def test_deterministic_bitwise():
             for x, y in zip(runs[0].peaks(0, d, wi), runs[1].peaks(0, d, wi)):
                 assert np.array_equal(x, y)
     assert runs[0].candidates() == runs[1].candidates()
+
+
+# ------------------------------------------------- plans, server, full size ----
+def test_plan_with_reduced_precision_matches_oracle():
+    """A batch plan whose band classes mix tensor-core (n_f >= 256, 2-D) and
+    FP32 segments at precision BF16: every segment against the oracle."""
+    shapes = [
+        dict(n_bl=2, n_ap=190, n_if=8, n_chan=32, n_dm=3, dm_step=20.0, windows=(1, 2, 4, 8, 16, 32)),
+        dict(n_bl=1, n_ap=170, n_if=8, n_chan=64, n_dm=3, dm_step=25.0, windows=(1, 4, 16)),
+        dict(n_bl=1, n_ap=120, n_if=8, n_chan=128, n_dm=2, dm_step=30.0, windows=(2, 8, 32)),
+        dict(n_bl=2, n_ap=210, n_if=4, n_chan=16, n_dm=4, dm_step=40.0, windows=(1, 2, 4, 8)),
+    ]
+    items = []
+    for i, sh in enumerate(shapes):
+        wl = synth.small(**sh, name=f"pmix{i}", min_baselines=1)
+        vis, cal, _ = make_data(wl, seed=400 + i)
+        items.append((wl, vis, cal))
+    dev = [torch.from_numpy(v).cuda() for _, v, _ in items]
+    plan = V.Plan([(wl, d, cal) for (wl, _, cal), d in zip(items, dev)], graph=True, autotune=True,
+                  precision=V.VOLKS_BF16)
+    plan.run(stream=torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    for i, (wl, vis, cal) in enumerate(items):
+        ref = O.search(wl, vis, cal)
+        r = plan.result(i)
+        n, ties, misses = check_peaks_prec(wl, r, ref, vis, cal, V.VOLKS_BF16)
+        assert misses <= 1
+        check_candidates_prec(wl, r, ref)
+    plan.close()
+
+
+def test_server_reduced_precision_alone_equals_mix():
+    """BF16 requests: each result in the continuous-batching mix equals the
+    same search run alone, bit for bit (deterministic kernels)."""
+    reqs = []
+    for i in range(6):
+        wl = synth.small(n_bl=1 + i % 2, n_ap=140 + 29 * i, n_if=8, n_chan=32 << (i % 2), n_dm=3,
+                         dm_step=30.0, windows=(1, 2, 4, 8, 16, 32), min_baselines=1, name=f"preq{i}")
+        vis, cal, _ = make_data(wl, seed=500 + i)
+        reqs.append((wl, vis, cal))
+    alone = []
+    for wl, vis, cal in reqs:
+        s = V.Search(wl, torch.from_numpy(vis).cuda(), cal, precision=V.VOLKS_BF16)
+        alone.append(s.candidates())
+        s.close()
+    srv = V.Server(max_inflight=3, hbm_budget_bytes=8 << 30)
+    devs = [torch.from_numpy(v).cuda() for _, v, _ in reqs]
+    ids = [srv.submit(wl, d, cal, precision=V.VOLKS_BF16) for (wl, _, cal), d in zip(reqs, devs)]
+    for i, rid in enumerate(ids):
+        info, got = srv.wait_all(rid)
+        assert info.status == 0
+        assert got == alone[i]
+    srv.close()
+
+
+def test_evn_full_size_bf16_sampled_parity():
+    """The EVN-scale scan (15 baselines x 58,594 APs x 512 points, 501 DM
+    trials, windows 1..32) searched at BF16 in the benchmark's launch
+    configuration: sampled segments against the oracle one by one, and the
+    whole candidate list and sampled series against the FP32 search."""
+    wl, vis_t, cal, pulses = synth.gen_evn_torch(seed=2)
+    stream = torch.cuda.current_stream().cuda_stream
+    g16 = V.Search(wl, vis_t, cal, stream=stream, precision=V.VOLKS_BF16)
+    c16 = g16.candidates()
+    g32 = V.Search(wl, vis_t, cal, stream=stream)
+    c32 = g32.candidates()
+    key = lambda c: (c["bl"], c["dm_idx"], c["win"], c["seg"], c["g0_ap"], c["g1_ap"], c["n_windows"])
+    k16, k32 = {key(c): c for c in c16}, {key(c): c for c in c32}
+    # a candidate can differ only through a coarse miss moving a series'
+    # statistics across a decision boundary: allow a handful in ~5e4
+    diff = set(k16) ^ set(k32)
+    assert len(diff) <= max(2, len(k32) // 1000), (len(diff), len(k32))
+    rng = np.random.default_rng(1)
+    shifts, _ = g16.shifts()
+    n_cmp = n_same = 0
+    for _ in range(12):
+        b, d = int(rng.integers(0, wl.n_bl)), int(rng.integers(0, wl.n_dm))
+        for wi in range(len(wl.windows)):
+            P16, q16, m16 = g16.peaks(b, d, wi)
+            P32, q32, m32 = g32.peaks(b, d, wi)
+            same = (q16 == q32) & (m16 == m32)
+            n_cmp += len(P16)
+            n_same += int(same.sum())
+            np.testing.assert_allclose(P16[same], P32[same], rtol=1e-5)
+    assert n_same >= n_cmp - max(3, n_cmp // 20000), (n_same, n_cmp)
+    # sampled segments against the FP64 oracle
+    for p in pulses[:3]:
+        b = int(rng.integers(0, wl.n_bl))
+        d = int(np.argmin(np.abs(wl.dms() - p.dm)))
+        Sb = vis_t[b].cpu().numpy()
+        X = O.calibrate(Sb, cal[b], wl.n_if, wl.n_chan, wl.chan_bw_mhz)
+        lo = (p.t0_ap // 32) * 32
+        Y = O.delay_transform(O.dedisperse(X, shifts[d])[lo:lo + 64], wl.pad_delay)
+        for wi, w in enumerate(wl.windows):
+            P, q, m = g16.peaks(b, d, wi)
+            pk = O.window_peaks(Y, w, wl.pad_rate)
+            s0 = lo // w
+            for j in range(min(len(pk.P), len(P) - s0)):
+                s = s0 + j
+                assert math.isclose(P[s], pk.P[j], rel_tol=P_REL), (b, d, w, s)
+                if (pk.P[j] - pk.P2[j]) / pk.P[j] >= TIE_REL:
+                    assert (q[s], m[s]) == (pk.q[j], pk.m[j]), (b, d, w, s)
+    g16.close()
+    g32.close()
