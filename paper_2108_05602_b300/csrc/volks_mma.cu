@@ -359,18 +359,28 @@ __device__ __forceinline__ void merge_block(uint32_t (&v)[4], uint32_t (&c)[4], 
   uint32_t bm = max(max(v[0], v[1]), max(v[2], v[3]));
   bm = __reduce_max_sync(0xffffffffu, bm);
   const uint32_t mx = max(runmax[sg], bm);
-  const uint32_t thr = __float_as_uint(__uint_as_float(mx) * Keep<PREC>::value);
-  const bool ko = lane < on && ov >= thr;
-  bool kn[4];
+  // margin: 1 - Keep, halved while more than kTopK cells pass (at most a few
+  // times; exact ties beyond kTopK fall through to the top-kTopK selection)
+  float keep = Keep<PREC>::value;
+  uint32_t thr;
+  bool ko, kn[4];
+  uint32_t bo, bn[4];
+  int total;
+#pragma unroll 1
+  for (int it = 0;; ++it) {
+    thr = __float_as_uint(__uint_as_float(mx) * keep);
+    ko = lane < on && ov >= thr;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) kn[i] = v[i] >= thr;
-  const uint32_t bo = __ballot_sync(0xffffffffu, ko);
-  uint32_t bn[4];
-  int total = __popc(bo);
+    for (int i = 0; i < 4; ++i) kn[i] = v[i] >= thr;
+    bo = __ballot_sync(0xffffffffu, ko);
+    total = __popc(bo);
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    bn[i] = __ballot_sync(0xffffffffu, kn[i]);
-    total += __popc(bn[i]);
+    for (int i = 0; i < 4; ++i) {
+      bn[i] = __ballot_sync(0xffffffffu, kn[i]);
+      total += __popc(bn[i]);
+    }
+    if (total <= kTopK || it == 6) break;
+    keep = 0.5f * (1.0f + keep);
   }
   __syncwarp();
   if (total <= kTopK) {
@@ -442,29 +452,20 @@ template <int L>
 __device__ __forceinline__ void drain_job(uint32_t tb, uint32_t* cm, int ch0, int ch1, uint64_t* empty,
                                           int lane) {
   constexpr int SEGC = 8 << L;  // columns per segment
-  auto fold = [&](const uint32_t (&v)[32], int ch) {
-    if constexpr (SEGC == 16) {
-      float m[2] = {0.f, 0.f};
+  static_assert(SEGC >= 32, "a chunk lies within one segment");
+  // max |Z|^2 over the 16 cells of a 32-column chunk, two independent chains
+  auto fold = [&](const uint32_t (&v)[32]) {
+    float ma = 0.f, mb = 0.f;
 #pragma unroll
-      for (int h = 0; h < 2; ++h)
-#pragma unroll
-        for (int i = 16 * h; i < 16 * h + 16; i += 4) {
-          const float a0 = __uint_as_float(v[i]), a1 = __uint_as_float(v[i + 1]);
-          const float a2 = __uint_as_float(v[i + 2]), a3 = __uint_as_float(v[i + 3]);
-          m[h] = tc::fmax3(m[h], fmaf(a0, a0, a1 * a1), fmaf(a2, a2, a3 * a3));
-        }
-      atomicMax(cm + (2 * ch) * kMRows, __float_as_uint(m[0]));
-      atomicMax(cm + (2 * ch + 1) * kMRows, __float_as_uint(m[1]));
-    } else {
-      float m = 0.f;
-#pragma unroll
-      for (int i = 0; i < 32; i += 4) {
-        const float a0 = __uint_as_float(v[i]), a1 = __uint_as_float(v[i + 1]);
-        const float a2 = __uint_as_float(v[i + 2]), a3 = __uint_as_float(v[i + 3]);
-        m = tc::fmax3(m, fmaf(a0, a0, a1 * a1), fmaf(a2, a2, a3 * a3));
-      }
-      atomicMax(cm + ((ch * 32) / SEGC) * kMRows, __float_as_uint(m));
+    for (int i = 0; i < 32; i += 8) {
+      const float a0 = __uint_as_float(v[i]), a1 = __uint_as_float(v[i + 1]);
+      const float a2 = __uint_as_float(v[i + 2]), a3 = __uint_as_float(v[i + 3]);
+      const float b0 = __uint_as_float(v[i + 4]), b1 = __uint_as_float(v[i + 5]);
+      const float b2 = __uint_as_float(v[i + 6]), b3 = __uint_as_float(v[i + 7]);
+      ma = tc::fmax3(ma, fmaf(a0, a0, a1 * a1), fmaf(a2, a2, a3 * a3));
+      mb = tc::fmax3(mb, fmaf(b0, b0, b1 * b1), fmaf(b2, b2, b3 * b3));
     }
+    return fmaxf(ma, mb);
   };
 #pragma unroll 1
   for (int ch = ch0; ch < ch1; ++ch) {
@@ -477,7 +478,7 @@ __device__ __forceinline__ void drain_job(uint32_t tb, uint32_t* cm, int ch0, in
       __syncwarp();
       if (lane == 0) mbar_arrive(empty);
     }
-    fold(v, ch);
+    atomicMax(cm + ((ch * 32) / SEGC) * kMRows, __float_as_uint(fold(v)));
   }
 }
 
@@ -668,7 +669,6 @@ __device__ __forceinline__ bool mma_tile(const UnitState& us, uint8_t* smem, Mma
         uint32_t* cm = colmax + sig_base(l) * kMRows + row;
         if (ok) {
           switch (l) {
-            case 1: drain_job<1>(tb, cm, ch0, ch1, &bars.empty[buf], lane); break;
             case 2: drain_job<2>(tb, cm, ch0, ch1, &bars.empty[buf], lane); break;
             case 3: drain_job<3>(tb, cm, ch0, ch1, &bars.empty[buf], lane); break;
             case 4: drain_job<4>(tb, cm, ch0, ch1, &bars.empty[buf], lane); break;
