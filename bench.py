@@ -38,7 +38,7 @@ SM_COUNT, FP32_LANES = 148, 128
 WORKLOADS = {
     # the EVN-scale scan the metric is quoted on
     "evn_fp32": lambda synth: synth.evn(),
-    # the same scan with the rate transform of the 2..32-AP windows as a
+    # the same scan with the rate transform of the 4..32-AP windows as a
     # tensor-core DFT GEMM (BF16 / FP16 / FP8 E4M3) + FP32 top-8 refinement
     "evn_bf16": lambda synth: synth.evn(),
     "evn_fp16": lambda synth: synth.evn(),
@@ -101,7 +101,7 @@ def mma_flops(wl, nvalid, precision) -> float:
     eb = 1 if precision == 3 else 2
     per_block = 0.0
     for w in wl.windows:
-        if w < 2:
+        if w < 4:
             continue
         seg_kb = 2 * w * eb
         if seg_kb >= 32:
@@ -116,10 +116,11 @@ def mma_flops(wl, nvalid, precision) -> float:
 
 def cuda_core_flops_mma(wl, nvalid) -> float:
     """Nominal CUDA-core flops of one search on the tensor-core kernel: the
-    FP32 delay transform and the 1-AP window as in algorithmic_flops; for
-    the GEMM windows (2..32 APs), 3 per coarse |Z|^2 cell (square, add,
-    max) plus the FP32 refinement of at most 8 delay cells per segment and
-    delay-residue unit (5 R log2 R + 3 R each)."""
+    FP32 delay transform and the 1- and 2-AP windows as in
+    algorithmic_flops; for the GEMM windows (4..32 APs), 3 per coarse
+    |Z|^2 cell (square, add, max) plus the FP32 refinement of at most 8
+    delay cells per segment and delay-residue unit (5 R log2 R + 3 R each,
+    counted at 8)."""
     M = wl.pad_delay * wl.n_f
     fold = max(1, wl.n_f // 512)
     units_per_seg = wl.pad_delay * fold
@@ -132,14 +133,26 @@ def cuda_core_flops_mma(wl, nvalid) -> float:
             R = 1 if w == 1 else 4 * w
             if w == 1:
                 tot += ns * M * 3.0
+            elif w == 2:
+                tot += ns * M * (5.0 * R * math.log2(R) + 3.0 * R)
             else:
                 tot += ns * (R * M * 3.0 + 8 * units_per_seg * (5.0 * R * math.log2(R) + 3.0 * R))
     return tot * wl.n_bl
 
 
-def kernel_source_hash() -> str:
+KERNEL_SOURCES = {
+    # the FP32 search kernel and the tensor-core search kernel: sources whose
+    # change invalidates a committed DRAM-traffic capture
+    "search_kernel_traffic.json": ("volks_kernels.cu", "search_common.cuh", "fft_regs.cuh", "twiddle_ce.h",
+                                   "volks_internal.h"),
+    "search_mma_kernel_traffic.json": ("volks_mma.cu", "tcgen05.cuh", "search_common.cuh", "fft_regs.cuh",
+                                       "twiddle_ce.h", "volks_internal.h"),
+}
+
+
+def kernel_source_hash(files) -> str:
     h = hashlib.sha256()
-    for f in ("volks_kernels.cu", "search_common.cuh", "fft_regs.cuh", "twiddle_ce.h", "volks_internal.h"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_2108_05602_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -159,18 +172,18 @@ def fp32_peak_tflops(peaks) -> tuple:
 
 
 def traffic_per_launch(workload_name):
-    """DRAM bytes (read + write) of one search-kernel launch from the
-    committed full-size ncu capture, or None if there is none for this
-    workload and the current kernel source."""
-    p = os.path.join(ROOT, "profiles", "search_kernel_traffic.json")
-    try:
-        with open(p) as f:
-            t = json.load(f)
-    except OSError:
-        return None
-    if t.get("kernel_hash") != kernel_source_hash() or t.get("workload") != workload_name:
-        return None
-    return t["dram_bytes_per_launch"]
+    """DRAM bytes (read + write) of one search-kernel launch from a committed
+    full-size ncu capture, or None if there is none for this workload and
+    the current kernel source."""
+    for name, files in KERNEL_SOURCES.items():
+        try:
+            with open(os.path.join(ROOT, "profiles", name)) as f:
+                t = json.load(f)
+        except OSError:
+            continue
+        if t.get("workload") == workload_name and t.get("kernel_hash") == kernel_source_hash(files):
+            return t["dram_bytes_per_launch"]
+    return None
 
 
 class ClockSampler:
@@ -367,6 +380,38 @@ def run_volks(args):
     _, e2e_max = shard.reduce_step(0.0, e2e_s, device="cuda")
     e2e_value = n_all / args.steps * e2e_steps / e2e_max
 
+    # the reduced-precision forms of the same search on the same scan (N = 1
+    # only): 1 warm-up + 2 timed steps each, CUDA events on the stream
+    forms = None
+    if prec == 0 and world == 1 and not args.no_forms and args.workload == "evn_fp32":
+        forms = {}
+        ref_keys = {(c["bl"], c["dm_idx"], c["win"], c["seg"], c["g0_ap"], c["g1_ap"]) for c in cands}
+        for name, pv in (("bf16", 1), ("fp8", 3)):
+            def fstep(x, pv=pv):
+                s = V.Search(wl, x, cal, stream=sptr, precision=pv)
+                c = s.candidates()
+                t = s.timing()
+                s.close()
+                return c, t
+            fstep(vis)
+            torch.cuda.synchronize()
+            fa, fb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            fa.record(stream)
+            kms, fc = [], []
+            for _ in range(2):
+                fc, tm = fstep(vis)
+                kms.append(tm.ms_search)
+            fb.record(stream)
+            torch.cuda.synchronize()
+            fms = fa.elapsed_time(fb) / 2
+            keys = {(c["bl"], c["dm_idx"], c["win"], c["seg"], c["g0_ap"], c["g1_ap"]) for c in fc}
+            mk = statistics.mean(kms)
+            forms[name] = {"value": trials / (fms / 1e3), "unit": UNIT, "ms_per_step": fms,
+                           "kernel_ms": mk, "vs_fp32": (trials / (fms / 1e3)) / value,
+                           "tensor_tflops": mma_flops(wl, nvalid, pv) / (mk / 1e3) / 1e12,
+                           "candidates": len(fc),
+                           "candidates_differing_from_fp32": len(keys ^ ref_keys)}
+
     if rank == 0:
         peaks = measured_peaks()
         peak, mhz = fp32_peak_tflops(peaks)
@@ -428,6 +473,8 @@ def run_volks(args):
             "clocks": clk.summary(),
             "candidates_per_step": len(cands),
         }
+        if forms is not None:
+            line["precision_forms"] = forms
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
@@ -620,6 +667,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="volks", choices=["volks", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the reduced-precision forms in the default EVN run")
     ap.add_argument("--workload", default="evn_fp32", choices=sorted(WORKLOADS) + ["batch64", "serving"])
     args = ap.parse_args()
     if args.impl == "reference":
