@@ -111,6 +111,54 @@ def calibrate(vis_b: np.ndarray, cal_b: Optional[np.ndarray], n_if: int, n_chan:
     return X
 
 
+# ------------------------------------------------ initial calibration ----
+@dataclass
+class CalFit:
+    tau_s: np.ndarray    # [n_if] delay dtau0^n
+    phi_rad: np.ndarray  # [n_if] phase dphi0^n in (-pi, pi]
+    cell: np.ndarray     # [n_if] signed delay cell of the peak
+    amp: np.ndarray      # [n_if] |G(peak)| / sum_j |S(j)| (1 for a perfect fringe)
+
+
+def fringe_fit_calibrator(vis_b: np.ndarray, n_if: int, n_chan: int, chan_bw_mhz: float,
+                          pad: int = 4) -> CalFit:
+    """Initial calibration (Sec. 2.1.1): fringe fit of a strong calibrator,
+    per IF n of one baseline, giving the (dtau0^n, dphi0^n) that the search
+    removes with exp(-i (2 pi f_j dtau0^n + dphi0^n)) (Eq. 1).
+
+      1. coherent integration over the scan: S(j) = sum_t vis[t, n J + j];
+      2. delay transform over the IF's J channels, zero-padded by `pad` (the
+         factor of Sec. 2.2): G(m) = sum_j S(j) exp(-2 pi i j m / (pad J));
+      3. peak m* = argmax |G|^2 (lowest cell on ties), signed in
+         [-pad J / 2, pad J / 2): dtau0 = m* / (pad J chan_bw);
+      4. phase at the peak, referenced to the channel centres f_j = (j + 1/2)
+         chan_bw: dphi0 = arg G(m*) - pi chan_bw dtau0, wrapped to (-pi, pi].
+    The delay is found on the transform grid (resolution 1 / (pad J chan_bw))
+    and is ambiguous modulo 1 / chan_bw."""
+    J = n_chan
+    Mc = pad * J
+    bw = chan_bw_mhz * 1e6
+    tau = np.zeros(n_if)
+    phi = np.zeros(n_if)
+    cell = np.zeros(n_if, dtype=np.int64)
+    amp = np.zeros(n_if)
+    for n in range(n_if):
+        S = vis_b[:, n * J:(n + 1) * J].astype(np.complex128).sum(axis=0)
+        G = np.fft.fft(S, n=Mc)
+        pw = G.real ** 2 + G.imag ** 2
+        m = int(np.argmax(pw))
+        ms = m - Mc if m >= Mc // 2 else m
+        tau[n] = ms / (Mc * bw)
+        ph = np.angle(G[m]) - np.pi * bw * tau[n]
+        phi[n] = math.remainder(ph, 2 * np.pi)
+        if phi[n] <= -np.pi:
+            phi[n] += 2 * np.pi
+        cell[n] = ms
+        tot = np.abs(S).sum()
+        amp[n] = abs(G[m]) / tot if tot > 0 else 0.0
+    return CalFit(tau, phi, cell, amp)
+
+
 # ---------------------------------------------------------------- a4 ----
 def dedisperse(X: np.ndarray, shifts_row: np.ndarray) -> np.ndarray:
     """a4: Xd[t, k] = X[t + shift_k, k] for t < n_valid."""

@@ -131,6 +131,37 @@ def draw_calibration(wl: Workload, rng: np.random.Generator) -> np.ndarray:
     return cal
 
 
+def calibrator_scan(wl: Workload, cal: np.ndarray, amp: float, rng: Optional[np.random.Generator],
+                    n_ap: Optional[int] = None) -> np.ndarray:
+    """A strong continuum calibrator: every AP carries amp * exp(i (2 pi f_j
+    dtau^n + dphi^n)) at channel j of IF n (f_j the channel-centre frequency
+    within the IF; (dtau, dphi) = cal[b, n]), plus unit noise when rng is
+    given.  complex64 [n_bl][n_ap][n_f]."""
+    n_ap = wl.n_ap if n_ap is None else n_ap
+    k = np.arange(wl.n_f)
+    n = k // wl.n_chan
+    j = k % wl.n_chan
+    f_j_hz = (j + 0.5) * wl.chan_bw_mhz * 1e6
+    ph = 2 * np.pi * f_j_hz[None, :] * cal[:, n, 0] + cal[:, n, 1]       # [n_bl][n_f]
+    sig = (amp * np.exp(1j * ph)).astype(np.complex64)
+    vis = np.broadcast_to(sig[:, None, :], (wl.n_bl, n_ap, wl.n_f)).copy()
+    if rng is not None:
+        vis += noise(wl, rng, n_ap)
+    return vis
+
+
+def draw_calibration_on_grid(wl: Workload, rng: np.random.Generator, pad: int = 4) -> np.ndarray:
+    """Per-baseline, per-IF (delay, phase) with the delay on the grid of a
+    pad-times zero-padded transform over one IF's channels, within
+    +-1 / (4 chan_bw)."""
+    Mc = pad * wl.n_chan
+    cells = rng.integers(-Mc // 4, Mc // 4, size=(wl.n_bl, wl.n_if))
+    cal = np.empty((wl.n_bl, wl.n_if, 2), dtype=np.float64)
+    cal[..., 0] = cells / (Mc * wl.chan_bw_mhz * 1e6)
+    cal[..., 1] = rng.uniform(-np.pi, np.pi, size=(wl.n_bl, wl.n_if))
+    return cal
+
+
 def pulse_footprint(wl: Workload, cal: np.ndarray, p: Pulse):
     """Return (rows [n_f, W], values [n_bl, n_f, W]) of one pulse.
 

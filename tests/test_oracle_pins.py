@@ -358,3 +358,69 @@ def test_pr1_pulse_recovered():
     same = np.sum(synth.arrival_offsets_ap(wl, 50.0) ==
                   O.shift_table(wl.f_lo_mhz, wl.chan_bw_mhz, wl.n_f, [51.0], wl.t_ap_s)[0])
     assert same >= 200
+
+
+# ------------------------------------------- initial calibration (Sec. 2.1.1) ----
+def test_calibrator_fit_recovers_on_grid_delay_and_phase_exactly():
+    """Noise-free calibrator with on-grid per-IF delays: the fit returns the
+    injected (dtau0, dphi0) and a perfect fringe amplitude."""
+    wl = synth.small(n_bl=2, n_ap=40, n_if=4, n_chan=32)
+    rng = np.random.default_rng(3)
+    cal = synth.draw_calibration_on_grid(wl, rng)
+    vis = synth.calibrator_scan(wl, cal, 0.7, None)
+    for b in range(wl.n_bl):
+        f = O.fringe_fit_calibrator(vis[b], wl.n_if, wl.n_chan, wl.chan_bw_mhz)
+        assert np.array_equal(f.tau_s, cal[b, :, 0])
+        dphi = np.angle(np.exp(1j * (f.phi_rad - cal[b, :, 1])))
+        assert np.max(np.abs(dphi)) < 1e-6
+        np.testing.assert_allclose(f.amp, 1.0, rtol=1e-6)
+        assert np.all((f.phi_rad > -np.pi) & (f.phi_rad <= np.pi))
+
+
+def test_calibrator_fit_flattens_the_fringe_phase_with_the_search_phasor():
+    """Applying the fitted table with the search's own calibration phasor
+    (Eq. 1) makes the time-integrated phase zero in every channel: a wrong
+    sign or channel-frequency reference in either would leave a slope."""
+    wl = synth.small(n_bl=1, n_ap=25, n_if=8, n_chan=16)
+    rng = np.random.default_rng(4)
+    cal = synth.draw_calibration_on_grid(wl, rng)
+    vis = synth.calibrator_scan(wl, cal, 1.3, None)
+    f = O.fringe_fit_calibrator(vis[0], wl.n_if, wl.n_chan, wl.chan_bw_mhz)
+    table = np.stack([f.tau_s, f.phi_rad], axis=1)
+    X = O.calibrate(vis[0], table, wl.n_if, wl.n_chan, wl.chan_bw_mhz, normalize=False)
+    ph = np.angle(X.sum(axis=0))
+    assert np.max(np.abs(ph)) < 1e-5
+
+
+def test_calibrator_fit_sign_offgrid_and_ambiguity():
+    wl = synth.small(n_bl=1, n_ap=10, n_if=1, n_chan=64)
+    bw = wl.chan_bw_mhz * 1e6
+    Mc = 4 * wl.n_chan
+    # a positive delay lands on a positive cell
+    cal = np.array([[[7 / (Mc * bw), 0.4]]])
+    f = O.fringe_fit_calibrator(synth.calibrator_scan(wl, cal, 1.0, None)[0], 1, 64, wl.chan_bw_mhz)
+    assert f.cell[0] == 7
+    # off grid: the nearest cell (within half a cell)
+    cal = np.array([[[-12.3 / (Mc * bw), -1.1]]])
+    f = O.fringe_fit_calibrator(synth.calibrator_scan(wl, cal, 1.0, None)[0], 1, 64, wl.chan_bw_mhz)
+    assert f.cell[0] == -12
+    # a delay one full period 1 / chan_bw away is the same fringe
+    cal = np.array([[[5 / (Mc * bw) + 1.0 / bw, 2.0]]])
+    f = O.fringe_fit_calibrator(synth.calibrator_scan(wl, cal, 1.0, None)[0], 1, 64, wl.chan_bw_mhz)
+    assert f.cell[0] == 5
+
+
+def test_calibrator_fit_in_noise_matches_expected_precision():
+    """Calibrator at amplitude 0.5 in unit noise over 200 APs x 32 channels:
+    delay on the right cell, phase error at the radiometer level."""
+    wl = synth.small(n_bl=3, n_ap=200, n_if=4, n_chan=32)
+    rng = np.random.default_rng(5)
+    cal = synth.draw_calibration_on_grid(wl, rng)
+    vis = synth.calibrator_scan(wl, cal, 0.5, rng)
+    # per IF: signal |sum| = 0.5 * 200 * 32, noise std of the sum's phase
+    sigma_phi = np.sqrt(2 * 200 * 32) / (0.5 * 200 * 32) / np.sqrt(2)
+    for b in range(wl.n_bl):
+        f = O.fringe_fit_calibrator(vis[b], wl.n_if, wl.n_chan, wl.chan_bw_mhz)
+        assert np.array_equal(f.tau_s, cal[b, :, 0])
+        dphi = np.angle(np.exp(1j * (f.phi_rad - cal[b, :, 1])))
+        assert np.max(np.abs(dphi)) < 6 * sigma_phi
