@@ -21,6 +21,14 @@ steps 3-6, then the detection criteria of Sec. 3.1.1):
   a9 window match (Sec. 3.1.1, item 2)
   a10 cross-baseline match (Sec. 3.1.1, item 3)
 
+and, around the search:
+
+  initial calibration: fringe fit of a calibrator scan per baseline and IF
+     (Sec. 2.1.1), giving the table a3 removes
+  localisation: least-squares position offset from the single pulse's
+     delays (Sec. 2.3, Eq. 2) with the baseline cuts and the leave-one-out
+     check of Sec. 3.1.2
+
 Library primitives used as steps: numpy's FFT (a5, a6), argmax, sort.
 
 Readings of points the paper leaves open (each also listed in the design
@@ -29,7 +37,11 @@ top channel centre and rounded half-up; frequency points at channel centres;
 Eq. 1's inner sum taken over all channels; normalisation by the per-channel
 RMS over the segment; f_ref = lower band edge; segments of w APs at stride w;
 normalised power rho = P / (w * N_eff) thresholded as a z-score over the
-(baseline, DM, window) series; matching by interval overlap.
+(baseline, DM, window) series; matching by interval overlap; the calibrator
+delay on the padded delay grid and its phase at the IF's first channel
+centre; the leave-one-out outlier flagged when its solution lies more than
+5x the median distance from the median solution (offsets compared in
+radians of RA and Dec as given).
 
 Every function is pinned by tests against closed forms, brute force or
 invariants (see tests/test_oracle_pins.py); none is "parity unpinned".
@@ -157,6 +169,64 @@ def fringe_fit_calibrator(vis_b: np.ndarray, n_if: int, n_chan: int, chan_bw_mhz
         tot = np.abs(S).sum()
         amp[n] = abs(G[m]) / tot if tot > 0 else 0.0
     return CalFit(tau, phi, cell, amp)
+
+
+# ------------------------------------------------------- localisation ----
+@dataclass
+class LocResult:
+    status: int                 # 0 solved, 1 fewer than min_baselines usable baselines
+    used: np.ndarray            # bool [n] baselines passing the SNR and length cuts
+    x: np.ndarray               # (dalpha, ddelta) rad from all used baselines
+    cov: np.ndarray             # 2x2: sigma^2 (A^T A)^-1, sigma^2 = RSS / (n - 2) (0 when n = 2)
+    rms_s: float                # rms delay residual
+    loo: np.ndarray             # [n_used][2]: solution without each used baseline (n_used >= 3)
+    outlier: int                # index into the input of the flagged baseline, or -1
+    x_clean: np.ndarray         # solution without the flagged baseline (= x when none)
+
+
+def localize(tau_s, tau_cal_s, dtau_dalpha, dtau_ddelta, snr, proj_len_m, min_snr=6.0,
+             max_proj_len_m=3.0e6, min_baselines=3, outlier_factor=5.0) -> LocResult:
+    """Single-pulse position offset from delays (Sec. 2.3, Eq. 2, with the
+    rules of Sec. 3.1.2).
+
+      1. keep baselines with SNR > min_snr and projected length
+         <= max_proj_len_m (longer ones have an ambiguous delay); at least
+         min_baselines must remain;
+      2. least squares for (dalpha, ddelta) in
+         tau - tau_cal = dtau/dalpha dalpha + dtau/ddelta ddelta;
+      3. leave-one-out: the solution without each baseline in turn; a bad
+         baseline makes every solution that includes it deviate, so the one
+         solution without it is the odd one out: with d_i the distance of the
+         i-th leave-one-out solution from their median, the baseline with the
+         largest d_i is flagged when d_i > outlier_factor * median(d) and at
+         least 4 baselines are used; the flagged baseline is dropped from
+         x_clean."""
+    tau_s, tau_cal_s = np.asarray(tau_s, float), np.asarray(tau_cal_s, float)
+    pa, pd = np.asarray(dtau_dalpha, float), np.asarray(dtau_ddelta, float)
+    used = (np.asarray(snr, float) > min_snr) & (np.abs(np.asarray(proj_len_m, float)) <= max_proj_len_m)
+    idx = np.nonzero(used)[0]
+    empty = np.zeros(2)
+    if len(idx) < max(min_baselines, 2):
+        return LocResult(1, used, empty, np.zeros((2, 2)), 0.0, np.zeros((0, 2)), -1, empty)
+    A = np.stack([pa[idx], pd[idx]], axis=1)
+    y = tau_s[idx] - tau_cal_s[idx]
+    x = np.linalg.lstsq(A, y, rcond=None)[0]
+    r = y - A @ x
+    n = len(idx)
+    s2 = float(r @ r) / (n - 2) if n > 2 else 0.0
+    cov = s2 * np.linalg.inv(A.T @ A)
+    loo = np.zeros((0, 2))
+    outlier, x_clean = -1, x.copy()
+    if n >= 3:
+        loo = np.stack([np.linalg.lstsq(np.delete(A, i, 0), np.delete(y, i), rcond=None)[0] for i in range(n)])
+        if n >= 4:
+            med = np.median(loo, axis=0)
+            d = np.hypot(loo[:, 0] - med[0], loo[:, 1] - med[1])
+            i = int(np.argmax(d))
+            if d[i] > outlier_factor * np.median(d):
+                outlier = int(idx[i])
+                x_clean = loo[i]
+    return LocResult(0, used, x, cov, float(np.sqrt(np.mean(r ** 2))), loo, outlier, x_clean)
 
 
 # ---------------------------------------------------------------- a4 ----

@@ -162,6 +162,29 @@ def draw_calibration_on_grid(wl: Workload, rng: np.random.Generator, pad: int = 
     return cal
 
 
+C_LIGHT = 299792458.0
+
+
+def loc_geometry(n_st: int, rng: np.random.Generator, ra0: float = 0.9, dec0: float = 0.6,
+                 gast: float = 1.3, max_len_m: float = 2.5e6):
+    """Synthetic VLBI geometry for localisation tests: n_st stations at
+    Earth-fixed positions (m) within max_len_m of each other, a priori
+    source direction (ra0, dec0) rad, Greenwich sidereal angle gast rad.
+    Returns (baseline vectors [n_bl][3], station index pairs)."""
+    pos = rng.uniform(-0.5, 0.5, size=(n_st, 3)) * (max_len_m / math.sqrt(3.0))
+    pairs = [(i, j) for i in range(n_st) for j in range(i + 1, n_st)]
+    B = np.array([pos[j] - pos[i] for i, j in pairs])
+    return B, pairs
+
+
+def geometric_delay(B: np.ndarray, ra: float, dec: float, gast: float) -> np.ndarray:
+    """tau = -B . s / c for the source unit vector s in the Earth-fixed frame
+    (hour angle gast - ra)."""
+    h = gast - ra
+    s = np.array([math.cos(dec) * math.cos(h), -math.cos(dec) * math.sin(h), math.sin(dec)])
+    return -(B @ s) / C_LIGHT
+
+
 def pulse_footprint(wl: Workload, cal: np.ndarray, p: Pulse):
     """Return (rows [n_f, W], values [n_bl, n_f, W]) of one pulse.
 

@@ -424,3 +424,79 @@ def test_calibrator_fit_in_noise_matches_expected_precision():
         assert np.array_equal(f.tau_s, cal[b, :, 0])
         dphi = np.angle(np.exp(1j * (f.phi_rad - cal[b, :, 1])))
         assert np.max(np.abs(dphi)) < 6 * sigma_phi
+
+
+# --------------------------------------------- localisation (Sec. 2.3, Eq. 2) ----
+def _loc_case(n_st=6, seed=0, noise_s=0.0, off=(2.0e-6, -1.5e-6)):
+    """Delays of a point source offset by `off` (rad) from the a priori
+    position, partials by central differences of the geometric delay."""
+    rng = np.random.default_rng(seed)
+    ra0, dec0, gast = 0.9, 0.6, 1.3
+    B, _ = synth.loc_geometry(n_st, rng, ra0, dec0, gast)
+    h = 1e-7
+    pa = (synth.geometric_delay(B, ra0 + h, dec0, gast) - synth.geometric_delay(B, ra0 - h, dec0, gast)) / (2 * h)
+    pd = (synth.geometric_delay(B, ra0, dec0 + h, gast) - synth.geometric_delay(B, ra0, dec0 - h, gast)) / (2 * h)
+    tau_cal = rng.uniform(-5e-9, 5e-9, size=len(B))
+    tau = (synth.geometric_delay(B, ra0 + off[0], dec0 + off[1], gast)
+           - synth.geometric_delay(B, ra0, dec0, gast) + tau_cal + rng.normal(0, noise_s, size=len(B)))
+    snr = np.full(len(B), 20.0)
+    length = np.linalg.norm(B, axis=1)
+    return tau, tau_cal, pa, pd, snr, length
+
+
+def test_localize_recovers_offsets_of_a_linear_model_exactly():
+    rng = np.random.default_rng(1)
+    pa, pd = rng.normal(0, 5e-3, 10), rng.normal(0, 5e-3, 10)
+    x_true = np.array([3e-6, -7e-6])
+    tau_cal = rng.normal(0, 1e-8, 10)
+    tau = tau_cal + pa * x_true[0] + pd * x_true[1]
+    r = O.localize(tau, tau_cal, pa, pd, np.full(10, 9.0), np.full(10, 1e6))
+    assert r.status == 0 and r.used.all() and r.outlier == -1
+    np.testing.assert_allclose(r.x, x_true, rtol=1e-9)
+    assert r.rms_s < 1e-20
+
+
+def test_localize_recovers_a_geometric_offset_and_the_sign_of_eq2():
+    """A source 0.4"/0.3" off the a priori position (geometric delays, not
+    the linear model): recovered to the linearisation error; a flipped sign
+    of tau - tau_cal would return the negated offset."""
+    off = (2.0e-6, -1.5e-6)
+    tau, tau_cal, pa, pd, snr, length = _loc_case(off=off)
+    r = O.localize(tau, tau_cal, pa, pd, snr, length)
+    assert r.status == 0
+    np.testing.assert_allclose(r.x, off, rtol=1e-4)
+
+
+def test_localize_applies_the_snr_and_length_cuts():
+    tau, tau_cal, pa, pd, snr, length = _loc_case(n_st=7, seed=2)
+    ref = O.localize(tau, tau_cal, pa, pd, snr, length)
+    tau2, snr2, len2 = tau.copy(), snr.copy(), length.copy()
+    tau2[0] += 1e-6; snr2[0] = 6.0          # SNR must exceed 6
+    tau2[1] -= 1e-6; len2[1] = 3.2e6        # projected baseline over 3000 km
+    r = O.localize(tau2, tau_cal, pa, pd, snr2, len2)
+    assert not r.used[0] and not r.used[1] and r.used[2:].all()
+    np.testing.assert_allclose(r.x, ref.x, rtol=1e-4)
+
+
+def test_localize_needs_three_baselines():
+    tau, tau_cal, pa, pd, snr, length = _loc_case(n_st=3, seed=3)
+    assert O.localize(tau, tau_cal, pa, pd, snr, length).status == 0
+    snr[2] = 2.0
+    r = O.localize(tau, tau_cal, pa, pd, snr, length)
+    assert r.status == 1
+
+
+def test_localize_leave_one_out_flags_a_bad_baseline():
+    """One baseline with a 30 ns fitting error (the RFI case of Sec. 3.1.2):
+    the leave-one-out solution without it is the odd one out, it is flagged,
+    and the clean solution recovers the offset; with no bad baseline nothing
+    is flagged."""
+    off = (2.0e-6, -1.5e-6)
+    tau, tau_cal, pa, pd, snr, length = _loc_case(n_st=6, seed=4, noise_s=0.05e-9, off=off)
+    r0 = O.localize(tau, tau_cal, pa, pd, snr, length)
+    assert r0.outlier == -1
+    tau[7] += 30e-9
+    r = O.localize(tau, tau_cal, pa, pd, snr, length)
+    assert r.outlier == 7
+    assert np.hypot(*(r.x_clean - off)) < 0.05 * np.hypot(*off)
+    assert np.hypot(*(r.x - off)) > 0.1 * np.hypot(*off)
