@@ -212,6 +212,29 @@ int volks_shift_table(double f_lo_mhz, double chan_bw_mhz, int32_t n_f, double t
 int volks_cross_match(const volks_candidate *in, size_t n, int32_t min_baselines,
                       volks_candidate *out, size_t cap, size_t *n_out);
 
+/*
+ * Initial calibration (Sec. 2.1.1): fringe fit of a strong calibrator scan
+ * giving, per baseline and IF, the (delay, phase) that volks_segment.cal
+ * takes (the search removes exp(-i (2 pi f_j dtau0^n + dphi0^n)), Eq. 1).
+ * seg: the calibrator scan, as for the search (vis device or host memory;
+ *      cal ignored).  Per (baseline b, IF n): the spectrum is integrated
+ *      coherently over the scan in FP64, transformed to delay over the IF's
+ *      n_chan channels zero-padded by `pad` (1, 2, 4 or 8; Sec. 2.2 uses 4),
+ *      and the largest |G| cell m* (lowest on ties, signed) gives
+ *      dtau0 = m* / (pad n_chan chan_bw) and dphi0 = arg G(m*) - pi chan_bw
+ *      dtau0 in (-pi, pi] (channel-centre frequencies).  The delay is on the
+ *      transform grid and ambiguous modulo 1 / chan_bw.
+ * cal_out: host, float64 [n_bl][n_if][2] = {dtau0 s, dphi0 rad}.
+ * amp_out: host, float64 [n_bl][n_if] = |G(m*)| / sum_j |S(j)| (1 for a
+ *      perfect fringe), or NULL.
+ * Runs on cuda_stream (device scratch stream-ordered) and waits for it.
+ * Errors: VOLKS_EINVAL (sizes as for the search, pad, pad * n_chan > 16384,
+ * n_bl > 65535),
+ * VOLKS_ENOMEM, VOLKS_ECUDA.
+ */
+int volks_fringe_fit_calibrator(const volks_segment *seg, int32_t pad, void *cuda_stream,
+                                double *cal_out, double *amp_out);
+
 /* ---- introspection, for checking each step against a reference ---- */
 
 /* Waits for the search.  Stage times and launch counts. */
@@ -369,6 +392,64 @@ int volks_server_get_stats(volks_server *srv, volks_server_stats *stats);
 int volks_server_drain(volks_server *srv, int32_t timeout_ms);
 /* Stops admitting, waits for running requests, frees everything. */
 void volks_server_free(volks_server *srv);
+
+/*
+ * Single-pulse localisation (Sec. 2.3, Eq. 2, with the rules of Sec.
+ * 3.1.2).  Host only, no device work.  One volks_loc_obs per baseline on
+ * which the pulse was fitted:
+ *   tau_s        residual delay of the pulse's fringe fit (s)
+ *   tau_cal_s    fine-calibration delay: the fringe-fit delay of a nearby
+ *                reference source on the same baseline (s)
+ *   dtau_dalpha, dtau_ddelta
+ *                partial derivatives of the geometric delay with respect to
+ *                right ascension and declination at the a priori position
+ *                (s/rad), supplied by the caller's geometry model
+ *   snr          the fit's SNR;  proj_len_m  the projected baseline length
+ * Baselines with snr > min_snr and |proj_len_m| <= max_proj_len_m are used
+ * (longer ones have an ambiguous delay); with fewer than min_baselines
+ * (>= 2) left, status = 1.  The offset x = (dalpha, ddelta) rad is the
+ * least-squares solution of tau - tau_cal = dtau/dalpha dalpha +
+ * dtau/ddelta ddelta over the used baselines (QR by modified Gram-Schmidt
+ * in FP64); status = 2 when their partials have numerical rank < 2
+ * (R22 <= 1e-12 max(R11, |column 2|)).  cov = sigma^2 (A^T A)^-1 with sigma^2 = RSS /
+ * (n - 2) (0 for n = 2), rms_s the rms residual.  Leave-one-out (n >= 3):
+ * the solution without each used baseline in turn; with n >= 4 and every
+ * such system of rank 2, d_i = distance of solution i from the
+ * coordinate-wise median of all of them, and the baseline with the largest
+ * d_i (first on ties) is flagged when d_i > outlier_factor * median(d)
+ * (a bad baseline perturbs every solution that includes it, so the one
+ * that excludes it stands out); x_clean is the solution without it (= x
+ * when none is flagged).
+ * obs: host, n entries.  used_out: host, n bytes (1 = used), or NULL.
+ * loo_out: host, float64 [n][2], row i = solution without baseline i for
+ * used baselines (NaN for unused ones or rank-deficient systems), or NULL.
+ * Errors: VOLKS_EINVAL (NULL obs/out with n > 0, n < 0, min_baselines < 2,
+ * a non-finite input on a used baseline).
+ */
+typedef struct {
+  double tau_s, tau_cal_s, dtau_dalpha, dtau_ddelta, snr, proj_len_m;
+} volks_loc_obs;
+
+typedef struct {
+  double min_snr;         /* 6 (Sec. 3.1.2) */
+  double max_proj_len_m;  /* 3.0e6 (Sec. 3.1.2) */
+  int32_t min_baselines;  /* 3 (Sec. 3.1.2) */
+  double outlier_factor;  /* 5 */
+} volks_loc_params;
+
+typedef struct {
+  int32_t status;         /* 0 solved, 1 too few baselines, 2 collinear partials */
+  int32_t n_used;
+  int32_t outlier;        /* index into obs of the flagged baseline, or -1 */
+  double x[2];            /* (dalpha, ddelta) rad, all used baselines */
+  double cov[4];          /* row-major 2x2 */
+  double rms_s;
+  double x_clean[2];
+} volks_loc_result;
+
+int volks_loc_default_params(volks_loc_params *p);
+int volks_localize(const volks_loc_obs *obs, int32_t n, const volks_loc_params *p,
+                   volks_loc_result *out, uint8_t *used_out, double *loo_out);
 
 /* ---- no-allocation variant ---------------------------------------------
  *

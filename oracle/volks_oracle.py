@@ -174,7 +174,8 @@ def fringe_fit_calibrator(vis_b: np.ndarray, n_if: int, n_chan: int, chan_bw_mhz
 # ------------------------------------------------------- localisation ----
 @dataclass
 class LocResult:
-    status: int                 # 0 solved, 1 fewer than min_baselines usable baselines
+    status: int                 # 0 solved, 1 fewer than min_baselines usable baselines,
+                                # 2 partials of the used baselines collinear (no unique solution)
     used: np.ndarray            # bool [n] baselines passing the SNR and length cuts
     x: np.ndarray               # (dalpha, ddelta) rad from all used baselines
     cov: np.ndarray             # 2x2: sigma^2 (A^T A)^-1, sigma^2 = RSS / (n - 2) (0 when n = 2)
@@ -194,13 +195,16 @@ def localize(tau_s, tau_cal_s, dtau_dalpha, dtau_ddelta, snr, proj_len_m, min_sn
          min_baselines must remain;
       2. least squares for (dalpha, ddelta) in
          tau - tau_cal = dtau/dalpha dalpha + dtau/ddelta ddelta;
+         (status 2 when the used baselines' partials have numerical rank
+         < 2: smallest singular value <= 1e-12 x the largest);
       3. leave-one-out: the solution without each baseline in turn; a bad
          baseline makes every solution that includes it deviate, so the one
          solution without it is the odd one out: with d_i the distance of the
          i-th leave-one-out solution from their median, the baseline with the
          largest d_i is flagged when d_i > outlier_factor * median(d) and at
-         least 4 baselines are used; the flagged baseline is dropped from
-         x_clean."""
+         least 4 baselines are used and every leave-one-out system has rank
+         2 (a rank-deficient one gets NaN rows and no baseline is flagged);
+         the flagged baseline is dropped from x_clean."""
     tau_s, tau_cal_s = np.asarray(tau_s, float), np.asarray(tau_cal_s, float)
     pa, pd = np.asarray(dtau_dalpha, float), np.asarray(dtau_ddelta, float)
     used = (np.asarray(snr, float) > min_snr) & (np.abs(np.asarray(proj_len_m, float)) <= max_proj_len_m)
@@ -210,7 +214,9 @@ def localize(tau_s, tau_cal_s, dtau_dalpha, dtau_ddelta, snr, proj_len_m, min_sn
         return LocResult(1, used, empty, np.zeros((2, 2)), 0.0, np.zeros((0, 2)), -1, empty)
     A = np.stack([pa[idx], pd[idx]], axis=1)
     y = tau_s[idx] - tau_cal_s[idx]
-    x = np.linalg.lstsq(A, y, rcond=None)[0]
+    x, _, rank, _ = np.linalg.lstsq(A, y, rcond=1e-12)
+    if rank < 2:
+        return LocResult(2, used, empty, np.zeros((2, 2)), 0.0, np.zeros((0, 2)), -1, empty)
     r = y - A @ x
     n = len(idx)
     s2 = float(r @ r) / (n - 2) if n > 2 else 0.0
@@ -218,8 +224,12 @@ def localize(tau_s, tau_cal_s, dtau_dalpha, dtau_ddelta, snr, proj_len_m, min_sn
     loo = np.zeros((0, 2))
     outlier, x_clean = -1, x.copy()
     if n >= 3:
-        loo = np.stack([np.linalg.lstsq(np.delete(A, i, 0), np.delete(y, i), rcond=None)[0] for i in range(n)])
-        if n >= 4:
+        loo = np.full((n, 2), np.nan)
+        for i in range(n):
+            xi, _, rk, _ = np.linalg.lstsq(np.delete(A, i, 0), np.delete(y, i), rcond=1e-12)
+            if rk == 2:
+                loo[i] = xi
+        if n >= 4 and np.isfinite(loo).all():
             med = np.median(loo, axis=0)
             d = np.hypot(loo[:, 0] - med[0], loo[:, 1] - med[1])
             i = int(np.argmax(d))

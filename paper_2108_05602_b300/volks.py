@@ -75,6 +75,22 @@ class volks_server_stats(C.Structure):
                 ("trials", C.c_int64), ("trials_per_s", C.c_double)]
 
 
+class volks_loc_obs(C.Structure):
+    _fields_ = [("tau_s", C.c_double), ("tau_cal_s", C.c_double), ("dtau_dalpha", C.c_double),
+                ("dtau_ddelta", C.c_double), ("snr", C.c_double), ("proj_len_m", C.c_double)]
+
+
+class volks_loc_params(C.Structure):
+    _fields_ = [("min_snr", C.c_double), ("max_proj_len_m", C.c_double),
+                ("min_baselines", C.c_int32), ("outlier_factor", C.c_double)]
+
+
+class volks_loc_result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("n_used", C.c_int32), ("outlier", C.c_int32),
+                ("x", C.c_double * 2), ("cov", C.c_double * 4), ("rms_s", C.c_double),
+                ("x_clean", C.c_double * 2)]
+
+
 _lib: Optional[C.CDLL] = None
 
 
@@ -147,8 +163,16 @@ def lib() -> C.CDLL:
     L.volks_search_peaks_noalloc.argtypes = [C.POINTER(volks_segment), C.POINTER(volks_params),
                                              P, P, P]
     L.volks_search_peaks_noalloc.restype = C.c_int
+    L.volks_fringe_fit_calibrator.argtypes = [C.POINTER(volks_segment), I32, P, C.POINTER(C.c_double),
+                                              C.POINTER(C.c_double)]
+    L.volks_fringe_fit_calibrator.restype = C.c_int
     L.volks_check_rate_gemm.argtypes = [P, I32, I32, I32, P]
     L.volks_check_rate_gemm.restype = C.c_int
+    L.volks_loc_default_params.argtypes = [C.POINTER(volks_loc_params)]
+    L.volks_loc_default_params.restype = C.c_int
+    L.volks_localize.argtypes = [C.POINTER(volks_loc_obs), I32, C.POINTER(volks_loc_params),
+                                 C.POINTER(volks_loc_result), P, P]
+    L.volks_localize.restype = C.c_int
     _lib = L
     return L
 
@@ -202,6 +226,27 @@ def volks_search_peaks_noalloc(seg: volks_segment, prm: volks_params, stream: in
            "volks_search_peaks_noalloc")
 
 
+def volks_fringe_fit_calibrator(wl, vis, pad: int = 4, stream: int = 0, n_bl=None, n_ap=None):
+    """Initial calibration from a calibrator scan (see include/volks.h):
+    returns (cal [n_bl][n_if][2] = (delay s, phase rad), amp [n_bl][n_if])."""
+    ptr, keep = _vis_pointer(vis)
+    seg = volks_segment()
+    seg.n_bl = wl.n_bl if n_bl is None else n_bl
+    seg.n_ap = wl.n_ap if n_ap is None else n_ap
+    seg.n_if, seg.n_chan = wl.n_if, wl.n_chan
+    seg.t_ap_s, seg.f_lo_mhz, seg.chan_bw_mhz = wl.t_ap_s, wl.f_lo_mhz, wl.chan_bw_mhz
+    seg.vis = ptr
+    seg.cal = None
+    cal = np.zeros((seg.n_bl, wl.n_if, 2), dtype=np.float64)
+    amp = np.zeros((seg.n_bl, wl.n_if), dtype=np.float64)
+    DP = C.POINTER(C.c_double)
+    _check(lib().volks_fringe_fit_calibrator(C.byref(seg), pad, C.c_void_p(stream),
+                                             cal.ctypes.data_as(DP), amp.ctypes.data_as(DP)),
+           "volks_fringe_fit_calibrator")
+    del keep
+    return cal, amp
+
+
 VOLKS_CHECK_SKIP_MMA = 1
 
 
@@ -211,6 +256,36 @@ def volks_check_rate_gemm(y_ptr: int, win: int, precision: int, out_ptr: int, fl
     [128][256]."""
     _check(lib().volks_check_rate_gemm(C.c_void_p(y_ptr), win, precision, flags,
                                        C.c_void_p(out_ptr)), "volks_check_rate_gemm")
+
+
+def volks_loc_default_params() -> volks_loc_params:
+    p = volks_loc_params()
+    _check(lib().volks_loc_default_params(C.byref(p)), "volks_loc_default_params")
+    return p
+
+
+def volks_localize(tau_s, tau_cal_s, dtau_dalpha, dtau_ddelta, snr, proj_len_m,
+                   prm: Optional[volks_loc_params] = None) -> dict:
+    """Single-pulse position offset from per-baseline delays (Eq. 2; see
+    include/volks.h).  Returns status, n_used, used [n] bool, x (dalpha,
+    ddelta) rad, cov 2x2, rms_s, loo [n][2], outlier (index or -1), x_clean."""
+    cols = [np.ascontiguousarray(a, dtype=np.float64).ravel()
+            for a in (tau_s, tau_cal_s, dtau_dalpha, dtau_ddelta, snr, proj_len_m)]
+    n = len(cols[0])
+    if any(len(c) != n for c in cols):
+        raise ValueError("per-baseline arrays differ in length")
+    obs = (volks_loc_obs * max(1, n))()
+    for i in range(n):
+        obs[i] = volks_loc_obs(*(float(c[i]) for c in cols))
+    prm = prm if prm is not None else volks_loc_default_params()
+    res = volks_loc_result()
+    used = np.zeros(max(1, n), dtype=np.uint8)
+    loo = np.zeros((max(1, n), 2), dtype=np.float64)
+    _check(lib().volks_localize(obs, n, C.byref(prm), C.byref(res), used.ctypes.data,
+                                loo.ctypes.data), "volks_localize")
+    return dict(status=res.status, n_used=res.n_used, used=used[:n].astype(bool),
+                x=np.array(res.x[:]), cov=np.array(res.cov[:]).reshape(2, 2), rms_s=res.rms_s,
+                loo=loo[:n], outlier=res.outlier, x_clean=np.array(res.x_clean[:]))
 
 
 def volks_cross_match(cands: Sequence[dict], min_baselines: int) -> List[dict]:

@@ -500,3 +500,20 @@ def test_localize_leave_one_out_flags_a_bad_baseline():
     assert r.outlier == 7
     assert np.hypot(*(r.x_clean - off)) < 0.05 * np.hypot(*off)
     assert np.hypot(*(r.x - off)) > 0.1 * np.hypot(*off)
+
+
+def test_localize_reports_collinear_partials():
+    """Eq. 2 has no unique solution when every baseline's partials are
+    proportional (one direction of the sky is unconstrained)."""
+    pa = np.array([1e-3, 2e-3, -3e-3, 4e-3])
+    r = O.localize(np.zeros(4), np.zeros(4), pa, 0.5 * pa, np.full(4, 10.0), np.full(4, 1e6))
+    assert r.status == 2
+    # three of four collinear: solvable, but one leave-one-out system is not
+    pd = 0.5 * pa
+    pd[3] = -pa[3]
+    x_true = np.array([1e-6, 2e-6])
+    tau = pa * x_true[0] + pd * x_true[1]
+    r = O.localize(tau, np.zeros(4), pa, pd, np.full(4, 10.0), np.full(4, 1e6))
+    assert r.status == 0 and r.outlier == -1
+    np.testing.assert_allclose(r.x, x_true, rtol=1e-9)
+    assert np.isnan(r.loo[3]).all() and np.isfinite(r.loo[:3]).all()
