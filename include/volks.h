@@ -62,16 +62,39 @@ extern "C" {
  * One scan segment: n_bl baselines x n_ap accumulation periods (APs) x
  * n_f = n_if * n_chan frequency points.  IFs are contiguous and searched as
  * one band (Sec. 2.2); frequency point k = n * n_chan + j of IF n, channel j
- * sits at f_lo_mhz + (k + 1/2) * chan_bw_mhz.
+ * sits at f_lo_mhz + (k + 1/2) * chan_bw_mhz.  n_f is a power of two in
+ * 64..2048 or three times one in 96..1536 (e.g. 12 IFs x 32 channels;
+ * mixed-radix delay transforms; those bands always search in FP32);
+ * volks_search_peaks_noalloc takes powers of two 64..512 only.
  *
- * vis: complex64 (interleaved float re, im), row-major [n_bl][n_ap][n_f].
- *      Device memory, or host memory (pageable or pinned; the library then
- *      copies it to the device on the call's stream).  Borrowed: it must
- *      stay valid and unchanged until volks_candidates() returns.
- * cal: host memory, float64 [n_bl][n_if][2] = {delay s, phase rad} of the
- *      initial calibration (Eq. 1: 2 pi f_j dtau0^n + dphi0^n, f_j the
- *      channel-centre frequency within the IF), or NULL for none.  Read
- *      during the call only.
+ * vis: complex64 (interleaved float re, im), row-major
+ *      [n_pol][n_bl][n_ap][n_f].  Device memory, or host memory (pageable
+ *      or pinned; the library then copies it to the device on the call's
+ *      stream).  Borrowed: it must stay valid and unchanged until
+ *      volks_candidates() returns.
+ * cal: host memory, float64 [n_pol][n_bl][n_if][2] = {delay s, phase rad}
+ *      of the initial calibration of each polarisation product (Eq. 1:
+ *      2 pi f_j dtau0^n + dphi0^n, f_j the channel-centre frequency within
+ *      the IF; Sec. 2.1.1 fits it per polarisation, baseline and IF), or
+ *      NULL for none.  Read during the call only.
+ * n_pol: polarisation products in vis, 1 (0 means 1) or 2 (e.g. LL and RR).
+ *      Each product is normalised and calibrated on its own, then the
+ *      products are summed coherently (Fig. 1: polarisations are combined
+ *      after the initial calibration), so the noise of a normalised cell
+ *      is n_pol times that of one product.
+ * autos, n_st, bl_st: the stations' auto spectra for the HOPS amplitude
+ *      normalisation (Sec. 2.2): |s_ij| / (mean a_i^2  mean a_j^2)^(1/4)
+ *      per frequency point and polarisation, the means over the segment's
+ *      APs in FP64.  autos: float32 [n_pol][n_st][n_ap][n_f] auto-spectrum
+ *      power, device or host memory, borrowed like vis; bl_st: host
+ *      int32 [n_bl][2], the two stations (i != j, < n_st) of each
+ *      baseline, read during the call only.  With autos NULL (n_st, bl_st
+ *      ignored) each frequency point is divided by the RMS of its cross
+ *      spectrum over the segment instead.  Only read when
+ *      volks_params.normalize_chan is 1.  A station whose auto power is 0
+ *      at a point zeroes that point on its baselines.
+ * Zero-initialise the struct: n_pol, n_st, bl_st and autos = 0 give one
+ * product and the cross-spectrum RMS normalisation.
  */
 typedef struct {
   int32_t n_bl, n_ap, n_if, n_chan;
@@ -80,6 +103,10 @@ typedef struct {
   double chan_bw_mhz;   /* channel width */
   const void *vis;
   const double *cal;
+  int32_t n_pol;        /* 0/1: one polarisation product; 2: two, combined */
+  int32_t n_st;         /* stations in autos */
+  const int32_t *bl_st; /* host [n_bl][2] station pair of each baseline */
+  const void *autos;    /* float32 [n_pol][n_st][n_ap][n_f], or NULL */
 } volks_segment;
 
 /*
@@ -94,8 +121,10 @@ typedef struct {
  * thresh: z-score threshold on normalised power (Sec. 3.1.1: 3).
  * min_windows / min_baselines: detection needs that many distinct windows on
  *      one baseline / distinct baselines (Sec. 3.1.1: 2 and 5).
- * normalize_chan: 1 divides each frequency point by its RMS over the
- *      segment (FP64), standing in for the HOPS normalisation (Sec. 2.2).
+ * normalize_chan: 1 applies the HOPS amplitude normalisation (Sec. 2.2)
+ *      with the segment's auto spectra, or, without them, divides each
+ *      frequency point by its cross-spectrum RMS over the segment (FP64);
+ *      0 leaves the amplitudes as they are.
  * skip_first_chan: 1 drops channel 0 of every IF (Eq. 1's inner sum read
  *      literally as j = 1 .. J-1).
  */
@@ -224,12 +253,14 @@ int volks_cross_match(const volks_candidate *in, size_t n, int32_t min_baselines
  *      dtau0 = m* / (pad n_chan chan_bw) and dphi0 = arg G(m*) - pi chan_bw
  *      dtau0 in (-pi, pi] (channel-centre frequencies).  The delay is on the
  *      transform grid and ambiguous modulo 1 / chan_bw.
- * cal_out: host, float64 [n_bl][n_if][2] = {dtau0 s, dphi0 rad}.
- * amp_out: host, float64 [n_bl][n_if] = |G(m*)| / sum_j |S(j)| (1 for a
- *      perfect fringe), or NULL.
+ * cal_out: host, float64 [n_pol][n_bl][n_if][2] = {dtau0 s, dphi0 rad}
+ *      (each polarisation product fitted on its own, Sec. 2.1.1), the
+ *      layout volks_segment.cal takes.
+ * amp_out: host, float64 [n_pol][n_bl][n_if] = |G(m*)| / sum_j |S(j)| (1
+ *      for a perfect fringe), or NULL.
  * Runs on cuda_stream (device scratch stream-ordered) and waits for it.
  * Errors: VOLKS_EINVAL (sizes as for the search, pad, pad * n_chan > 16384,
- * n_bl > 65535),
+ * n_pol * n_bl > 65535),
  * VOLKS_ENOMEM, VOLKS_ECUDA.
  */
 int volks_fringe_fit_calibrator(const volks_segment *seg, int32_t pad, void *cuda_stream,
@@ -256,8 +287,9 @@ int volks_result_peaks(volks_result *res, int32_t bl, int32_t dm_idx,
 int volks_result_stats(volks_result *res, int32_t bl, int32_t dm_idx,
                        int32_t win_idx, double *mean, double *std);
 
-/* Waits for the search.  Complex64 gains [n_bl][n_f] (calibration phasor
- * divided by the channel RMS) applied before dedispersion. */
+/* Waits for the search.  Complex64 gains [n_pol][n_bl][n_f] (calibration
+ * phasor times the amplitude normalisation: 1 / channel RMS, or the HOPS
+ * factor with auto spectra) applied before dedispersion. */
 int volks_result_gains(volks_result *res, float *gains, size_t cap_floats);
 
 /*
@@ -291,7 +323,8 @@ int volks_check_rate_gemm(const void *y, int32_t win, int32_t precision, int32_t
  * Results are those of volks_search_segment on each segment.
  *
  * volks_plan_create: validates every (segment, params) pair; visibilities
- *   must be device memory.  peak_budget_bytes > 0 bounds the per-trial peak
+ *   and auto spectra must be device memory (every run reads the auto
+ *   spectra at the pointer given here).  peak_budget_bytes > 0 bounds the per-trial peak
  *   buffers (8 bytes per trial) of the whole plan: segments whose peaks do
  *   not fit are processed in DM chunks (rounds), reusing their buffers;
  *   <= 0 keeps all DMs resident.  flags: VOLKS_PLAN_AUTOTUNE times the
@@ -342,11 +375,12 @@ void volks_plan_free(volks_plan *plan);
  * segment], so pulses crossing a segment boundary are searched whole; the
  * candidates' AP indices then count from the start of that extended input,
  * which begins at stream AP volks_request_info.ap_offset.  All segments of
- * a stream need the same n_bl and n_f, at least H APs and no larger sweep.
+ * a stream need the same n_bl and n_f, at least H APs and no larger sweep,
+ * one polarisation product and no auto spectra (VOLKS_EINVAL otherwise).
  * stream_id < 0: the segment is searched alone.
  *
- * vis (host or device) must stay valid until the request is collected;
- * cal is copied at submission.  volks_server_wait blocks up to timeout_ms
+ * vis and autos (host or device) must stay valid until the request is
+ * collected; cal and bl_st are copied at submission.  volks_server_wait blocks up to timeout_ms
  * (VOLKS_ETIMEOUT after that), then returns the candidates and removes the
  * request.  A request larger than the whole budget is refused at
  * submission (VOLKS_ENOMEM); a request whose search fails is reported by
@@ -482,8 +516,10 @@ int volks_localize(const volks_loc_obs *obs, int32_t n, const volks_loc_params *
  *
  * Returns VOLKS_EINVAL (nothing launched) for a segment whose scratch
  * (about 8 bytes per visibility + 8 bytes per output entry + tables)
- * exceeds VOLKS_NOALLOC_SCRATCH_BYTES, or for the descriptors
- * volks_search_segment rejects; VOLKS_ECUDA if a launch fails.  Returns
+ * exceeds VOLKS_NOALLOC_SCRATCH_BYTES, for two polarisation products or
+ * auto spectra (one product, cross-spectrum normalisation only), or for
+ * the descriptors volks_search_segment rejects; VOLKS_ECUDA if a launch
+ * fails.  Returns
  * without waiting for the device.
  *
  * All calls on a device share the one scratch array, which keeps the

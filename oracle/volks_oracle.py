@@ -10,8 +10,10 @@ computes, in the order the paper gives (Sec. 2.4.2 "Code optimization",
 steps 3-6, then the detection criteria of Sec. 3.1.1):
 
   a1 dedispersion shift table (per-frequency integer AP shift, Sec. 2.4.2)
-  a2 amplitude normalisation (HOPS/Mk4 style, Sec. 2.2)
-  a3 initial calibration phasor (Eq. 1, second line; Sec. 2.1.1)
+  a2 amplitude normalisation (HOPS/Mk4 style with the stations' auto spectra,
+     else the cross-spectrum RMS, Sec. 2.2), per polarisation product
+  a3 initial calibration phasor (Eq. 1, second line; Sec. 2.1.1), per
+     polarisation product, then the products summed (Fig. 1)
   a4 dedispersion (step 4)
   a5 delay transform: FFT along frequency, zero-padded by 4 (step 5, Sec. 2.2)
   a6 window combine and fringe-rate transform (step 6; the 2-D "geodetic"
@@ -107,16 +109,29 @@ def calib_phasor(cal_b: Optional[np.ndarray], n_if: int, n_chan: int,
     return np.exp(-1j * (2 * np.pi * f_j * cal_b[n, 0] + cal_b[n, 1]))
 
 
+def auto_norm(autos_i: np.ndarray, autos_j: np.ndarray) -> np.ndarray:
+    """a2 with auto spectra, the HOPS amplitude normalisation (Sec. 2.2):
+    |s~_ij| = |s_ij| / (mean a_i^2  mean a_j^2)^(1/4) per frequency point,
+    means over the segment's APs (FP64).  Returns the factor
+    (mean a_i^2 mean a_j^2)^(-1/4); 0 where either station has no power."""
+    Ai = np.mean(autos_i.astype(np.float64) ** 2, axis=0)
+    Aj = np.mean(autos_j.astype(np.float64) ** 2, axis=0)
+    prod = Ai * Aj
+    return np.where(prod > 0, np.where(prod > 0, prod, 1.0) ** -0.25, 0.0)
+
+
 def calibrate(vis_b: np.ndarray, cal_b: Optional[np.ndarray], n_if: int, n_chan: int,
               chan_bw_mhz: float, normalize: bool = True,
-              skip_first_chan: bool = False) -> np.ndarray:
-    """Steps a2+a3 applied to one baseline: X = S / rms_k * phasor_k.
-    A channel with zero power contributes zero."""
+              skip_first_chan: bool = False, norm: Optional[np.ndarray] = None) -> np.ndarray:
+    """Steps a2+a3 applied to one baseline: X = S * norm_k * phasor_k, with
+    norm_k = 1 / rms_k of the cross spectrum, or the given factors (e.g.
+    auto_norm).  A channel with zero power contributes zero."""
     X = vis_b.astype(np.complex128)
     if normalize:
-        rms = chan_rms(vis_b)
-        inv = np.where(rms > 0, 1.0 / np.where(rms > 0, rms, 1.0), 0.0)
-        X = X * inv[None, :]
+        if norm is None:
+            rms = chan_rms(vis_b)
+            norm = np.where(rms > 0, 1.0 / np.where(rms > 0, rms, 1.0), 0.0)
+        X = X * np.asarray(norm, dtype=np.float64)[None, :]
     X = X * calib_phasor(cal_b, n_if, n_chan, chan_bw_mhz)[None, :]
     if skip_first_chan:
         X[:, (np.arange(n_if * n_chan) % n_chan) == 0] = 0
@@ -411,26 +426,51 @@ def signed(i: int, n: int) -> int:
     return i - n if i >= (n + 1) // 2 and n > 1 else i
 
 
+def prepare(vis_pols: np.ndarray, cal_pols: Optional[np.ndarray], b: int, n_if: int, n_chan: int,
+            chan_bw_mhz: float, normalize: bool = True, skip_first_chan: bool = False,
+            autos: Optional[np.ndarray] = None, bl_st: Optional[np.ndarray] = None) -> np.ndarray:
+    """a2+a3 for baseline b with its polarisation products combined: each
+    product vis_pols[p, b] normalised (auto spectra autos[p, station] when
+    given, else the cross-spectrum RMS) and calibrated with its own table
+    cal_pols[p, b], then summed coherently (Fig. 1: the products are combined
+    after the initial calibration)."""
+    X = 0
+    for p in range(vis_pols.shape[0]):
+        norm = None
+        if autos is not None and normalize:
+            i, j = int(bl_st[b][0]), int(bl_st[b][1])
+            norm = auto_norm(autos[p, i], autos[p, j])
+        X = X + calibrate(vis_pols[p, b], None if cal_pols is None else cal_pols[p, b], n_if, n_chan,
+                          chan_bw_mhz, normalize, skip_first_chan, norm)
+    return X
+
+
 def search(wl, vis: np.ndarray, cal: Optional[np.ndarray], *,
            normalize: bool = True, skip_first_chan: bool = False,
            with_second: bool = True, baselines: Optional[Sequence[int]] = None,
-           dm_indices: Optional[Sequence[int]] = None) -> SearchResult:
-    """The whole search (a1..a10) on one scan segment vis[b, t, k].
+           dm_indices: Optional[Sequence[int]] = None, autos: Optional[np.ndarray] = None,
+           bl_st: Optional[np.ndarray] = None) -> SearchResult:
+    """The whole search (a1..a10) on one scan segment vis[b, t, k] (one
+    polarisation product, cal[b, n, 2]) or vis[p, b, t, k] (several,
+    cal[p, b, n, 2]); autos[p, station, t, k] with bl_st[b] = (i, j) select
+    the HOPS normalisation.
 
     ``wl`` carries n_if, n_chan, n_ap, t_ap_s, f_lo_mhz, chan_bw_mhz, dms(),
     windows, pad_delay, pad_rate, thresh, min_windows, min_baselines."""
+    vis_pols = vis if vis.ndim == 4 else vis[None]
+    cal_pols = None if cal is None else (cal if np.ndim(cal) == 4 else np.asarray(cal)[None])
     n_f = wl.n_if * wl.n_chan
     dms = wl.dms()
     shifts = shift_table(wl.f_lo_mhz, wl.chan_bw_mhz, n_f, dms, wl.t_ap_s)
-    nval = np.array([n_valid(vis.shape[1], r) for r in shifts])
+    nval = np.array([n_valid(vis_pols.shape[2], r) for r in shifts])
     res = SearchResult(shifts=shifts, nvalid=nval)
     n_eff = n_f - (wl.n_if if skip_first_chan else 0)
     M = wl.pad_delay * n_f
-    bls = range(vis.shape[0]) if baselines is None else baselines
+    bls = range(vis_pols.shape[1]) if baselines is None else baselines
     dis = range(len(dms)) if dm_indices is None else dm_indices
     for b in bls:
-        X = calibrate(vis[b], None if cal is None else cal[b], wl.n_if, wl.n_chan,
-                      wl.chan_bw_mhz, normalize, skip_first_chan)
+        X = prepare(vis_pols, cal_pols, b, wl.n_if, wl.n_chan, wl.chan_bw_mhz, normalize,
+                    skip_first_chan, autos, bl_st)
         for d in dis:
             Xd = dedisperse(X, shifts[d])
             Y = delay_transform(Xd, wl.pad_delay)

@@ -95,4 +95,36 @@ __device__ __forceinline__ void fft_dif(float2 (&x)[N]) {
 template <int N>
 __device__ __forceinline__ float2 fft_out(const float2 (&x)[N], int k) { return x[bitrev(k, ilog2(N))]; }
 
+// In-place FFT of N = 3 Q points (Q a power of two) held in registers,
+// natural-order output.  Cooley-Tukey with the factor 3 outermost:
+//   F_n1[k2]      = sum_{n2<Q} x[3 n2 + n1] W_Q^{n2 k2}          (3 Q-point FFTs)
+//   X[k2 + Q k1]  = sum_{n1<3} W_3^{n1 k1} (W_N^{n1 k2} F_n1[k2])  (Q 3-point DFTs)
+// with the 3-point DFT of (a, b, c): X0 = a + (b + c),
+// X1,2 = a - (b + c)/2 -+ i sin(2 pi/3) (b - c).
+template <int N>
+__device__ __forceinline__ void fft3_nat(float2 (&x)[N]) {
+  static_assert(N % 3 == 0 && ((N / 3) & (N / 3 - 1)) == 0, "N = 3 * 2^a");
+  constexpr int Q = N / 3;
+  constexpr float h = float(sin2pi(1, 3));
+  float2 f[3][Q];
+  static_for<0, 3>([&](auto a1) {
+    static_for<0, Q>([&](auto a2) {
+      f[decltype(a1)::value][decltype(a2)::value] = x[3 * decltype(a2)::value + decltype(a1)::value];
+    });
+    if constexpr (Q > 1) fft_dif<Q>(f[decltype(a1)::value]);
+  });
+  static_for<0, Q>([&](auto kk) {
+    constexpr int K2 = decltype(kk)::value;
+    constexpr int P = bitrev(K2, ilog2(Q));
+    const float2 a = f[0][P];
+    const float2 b = twiddle<N, K2>(f[1][P]);
+    const float2 c = twiddle<N, 2 * K2>(f[2][P]);
+    const float2 sum = cadd(b, c), dif = csub(b, c);
+    const float2 t = make_float2(fmaf(-0.5f, sum.x, a.x), fmaf(-0.5f, sum.y, a.y));
+    x[K2] = cadd(a, sum);
+    x[K2 + Q] = make_float2(fmaf(h, dif.y, t.x), fmaf(-h, dif.x, t.y));      // t - i h dif
+    x[K2 + 2 * Q] = make_float2(fmaf(-h, dif.y, t.x), fmaf(h, dif.x, t.y));  // t + i h dif
+  });
+}
+
 }  // namespace vk

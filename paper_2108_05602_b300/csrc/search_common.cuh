@@ -131,7 +131,8 @@ struct UnitState {
 // independent N-point FFTs, N = n_f / FOLD:
 //   Y[P c + r] = sum_{k<N} W_M^{k r} (sum_{f<FOLD} X[k + N f] W_P^{f r}) W_N^{k c},
 // so a unit computes the delay cells m = P c + r (c < N) of its residue r.
-// N = 32 * N1; the CTA has N threads.
+// N = 32 * N1 (N1 a power of two, or 3 times one for bands of 3 * 2^a
+// points); the CTA has N threads.
 //   stage 0  lane = AP, warp owns k0 = warp*KPW + j: gather xn[k][t + shift_k],
 //            fold and pre-twiddle
 //   stage 1  N1-point FFTs over k1 (k = k0 + 32 k1), twiddle W_N^{k0 m1}
@@ -143,7 +144,10 @@ struct UnitState {
 template <int N1, int FOLD>
 __device__ __forceinline__ void delay_stage(const UnitState& us, float2* S) {
   constexpr int N = 32 * N1;
-  constexpr int KPW = 32 / N1;
+  // N1 a power of two (radix-2 register FFTs, each warp owns 32 / N1
+  // consecutive k0) or 3 times one (mixed-radix FFTs, k0 = warp + N1 j)
+  constexpr bool kPow2 = (N1 & (N1 - 1)) == 0;
+  constexpr int KPW = (32 + N1 - 1) / N1;
   constexpr int LD = N + 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // ---- stage 0 + 1 ----
@@ -164,7 +168,8 @@ __device__ __forceinline__ void delay_stage(const UnitState& us, float2* S) {
     });
     static_for<0, KPW>([&](auto jj) {
       constexpr int J = decltype(jj)::value;
-      const int k0 = warp * KPW + J;
+      const int k0 = kPow2 ? warp * KPW + J : warp + N1 * J;
+      if (!kPow2 && k0 >= 32) return;
       float2 x[N1];
       static_for<0, N1>([&](auto kk1) {
         constexpr int K1 = decltype(kk1)::value;
@@ -184,10 +189,14 @@ __device__ __forceinline__ void delay_stage(const UnitState& us, float2* S) {
         if (r != 0) v = cmul(v, __ldg(tw_m + k * r));  // k < N, r < P: k r < M
         x[K1] = v;
       });
-      fft_dif<N1>(x);
+      if constexpr (kPow2) {
+        fft_dif<N1>(x);
+      } else {
+        fft3_nat<N1>(x);
+      }
       static_for<0, N1>([&](auto mm1) {
         constexpr int M1 = decltype(mm1)::value;
-        float2 v = x[bitrev(M1, ilog2(N1))];
+        float2 v = x[kPow2 ? bitrev(M1, ilog2(N1)) : M1];
         // W_N^{k0 m1} = W_{n_f}^{k0 m1 FOLD}
         if constexpr (M1 != 0) v = cmul(v, __ldg(tw_n + k0 * M1 * FOLD));  // < 32 N1 FOLD = n_f
         S[lane * LD + k0 * N1 + M1] = v;

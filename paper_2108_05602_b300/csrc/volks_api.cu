@@ -82,13 +82,26 @@ int validate(const volks_segment* s, const volks_params* p) {
   if (s->n_bl < 0 || s->n_ap < 0) return fail(VOLKS_EINVAL, "negative n_bl or n_ap");
   if (s->n_if < 1 || s->n_chan < 1) return fail(VOLKS_EINVAL, "n_if and n_chan must be >= 1");
   const long long n_f = (long long)s->n_if * s->n_chan;
-  if (!is_pow2(n_f) || n_f < 64 || n_f > 2048)
-    return fail(VOLKS_EINVAL, "n_if*n_chan = %lld: this build supports powers of two 64..2048", n_f);
+  const bool pow2_band = is_pow2(n_f) && n_f >= 64 && n_f <= 2048;
+  const bool mixed_band = n_f % 3 == 0 && is_pow2(n_f / 3) && n_f >= 96 && n_f <= 1536;
+  if (!pow2_band && !mixed_band)
+    return fail(VOLKS_EINVAL,
+                "n_if*n_chan = %lld: this build supports powers of two 64..2048 and 3 x powers of two 96..1536",
+                n_f);
   if (!(std::isfinite(s->t_ap_s) && s->t_ap_s > 0)) return fail(VOLKS_EINVAL, "t_ap_s must be > 0");
   if (!(std::isfinite(s->chan_bw_mhz) && s->chan_bw_mhz > 0))
     return fail(VOLKS_EINVAL, "chan_bw_mhz must be > 0");
   if (!(std::isfinite(s->f_lo_mhz) && s->f_lo_mhz > 0)) return fail(VOLKS_EINVAL, "f_lo_mhz must be > 0");
   if ((long long)s->n_bl * s->n_ap > 0 && !s->vis) return fail(VOLKS_EINVAL, "vis is NULL");
+  if (s->n_pol < 0 || s->n_pol > 2) return fail(VOLKS_EINVAL, "n_pol = %d: 1 or 2 products (0 means 1)", s->n_pol);
+  if (s->autos && p && p->normalize_chan == 1 && (long long)s->n_bl * s->n_ap > 0) {
+    if (s->n_st < 2 || !s->bl_st) return fail(VOLKS_EINVAL, "auto spectra need n_st >= 2 and bl_st");
+    for (int b = 0; b < s->n_bl; ++b) {
+      const int i = s->bl_st[2 * b], j = s->bl_st[2 * b + 1];
+      if (i < 0 || j < 0 || i >= s->n_st || j >= s->n_st || i == j)
+        return fail(VOLKS_EINVAL, "bl_st[%d] = (%d, %d): two different stations < n_st = %d", b, i, j, s->n_st);
+    }
+  }
   if (p->n_dm < 0) return fail(VOLKS_EINVAL, "n_dm < 0");
   if (!std::isfinite(p->dm_lo) || !std::isfinite(p->dm_step)) return fail(VOLKS_EINVAL, "DM grid not finite");
   if (p->n_dm > 0 && (p->dm_lo < 0 || p->dm_lo + p->dm_step * (p->n_dm - 1) < 0))
@@ -196,18 +209,27 @@ int SegJob::init(const volks_segment& s, const volks_params& p, int chunk) {
   int rc = shift_table(s.f_lo_mhz, s.chan_bw_mhz, n_f, s.t_ap_s, s.n_ap, p.dm_lo, p.dm_step, p.n_dm,
                        shifts.data(), nvalid.data());
   if (rc) return rc;
-  h_phasor.resize((size_t)s.n_bl * n_f);
-  for (int b = 0; b < s.n_bl; ++b)
+  n_pol = s.n_pol == 2 ? 2 : 1;
+  use_autos = s.autos != nullptr && p.normalize_chan == 1 && !empty;
+  n_rows = n_pol * (use_autos ? s.n_st : s.n_bl);
+  const size_t n_pb = (size_t)n_pol * s.n_bl;
+  h_phasor.resize(n_pb * n_f);
+  for (size_t pb = 0; pb < n_pb; ++pb)
     for (int k = 0; k < n_f; ++k) {
       const int n = k / s.n_chan, j = k % s.n_chan;
       double ph = 0.0;
       if (s.cal) {
         const double fj = (j + 0.5) * s.chan_bw_mhz * 1e6;
-        ph = kTwoPi * fj * s.cal[((size_t)b * s.n_if + n) * 2 + 0] + s.cal[((size_t)b * s.n_if + n) * 2 + 1];
+        ph = kTwoPi * fj * s.cal[(pb * s.n_if + n) * 2 + 0] + s.cal[(pb * s.n_if + n) * 2 + 1];
       }
-      h_phasor[(size_t)b * n_f + k] = make_double2(std::cos(ph), -std::sin(ph));
+      h_phasor[pb * n_f + k] = make_double2(std::cos(ph), -std::sin(ph));
     }
-  seg.cal = nullptr;  // the calibration table is read during the creating call only
+  h_blst.clear();
+  if (use_autos)
+    for (int b = 0; b < s.n_bl; ++b) h_blst.push_back(make_int2(s.bl_st[2 * b], s.bl_st[2 * b + 1]));
+  // the calibration table and station pairs are read during the creating call only
+  seg.cal = nullptr;
+  seg.bl_st = nullptr;
   h_tw_n.resize(n_f);
   for (int i = 0; i < n_f; ++i)
     h_tw_n[i] = make_float2((float)std::cos(kTwoPi * i / n_f), (float)-std::sin(kTwoPi * i / n_f));
@@ -218,9 +240,16 @@ int SegJob::init(const volks_segment& s, const volks_params& p, int chunk) {
   return 0;
 }
 
+size_t SegJob::input_bytes() const {
+  size_t b = (size_t)n_pol * seg.n_bl * seg.n_ap * n_f * sizeof(float2);
+  if (use_autos) b += (size_t)n_pol * seg.n_st * seg.n_ap * n_f * sizeof(float);
+  return b;
+}
+
 size_t SegJob::device_bytes() const {
   const size_t vis_n = (size_t)seg.n_bl * seg.n_ap * n_f;
-  return vis_n * 8 + (size_t)seg.n_bl * n_tchunk * n_f * 8 + (size_t)seg.n_bl * n_f * 24 +
+  return vis_n * 8 + (size_t)n_rows * n_tchunk * n_f * 8 + (size_t)n_pol * seg.n_bl * n_f * 24 +
+         (size_t)seg.n_bl * 8 +
          (size_t)prm.n_dm * (n_f + 1) * 4 + (size_t)(n_f + M) * 8 + keys_bytes_per_dm() * dm_chunk +
          (size_t)seg.n_bl * prm.n_dm * prm.n_win * 16 + (size_t)seg.n_bl * dm_chunk * word_per_bd * 4 +
          (size_t)cap * sizeof(DevCand) + 4;
@@ -237,9 +266,10 @@ int SegJob::alloc(cudaStream_t s, bool ordered) {
   if (empty) return 0;
   const size_t vis_n = (size_t)seg.n_bl * seg.n_ap * n_f;
   VK_A(d_xn, vis_n, "alloc normalised copy");
-  VK_A(d_part, (size_t)seg.n_bl * n_tchunk * n_f, "alloc partial sums");
-  VK_A(d_phasor, (size_t)seg.n_bl * n_f, "alloc phasor");
-  VK_A(d_gain, (size_t)seg.n_bl * n_f, "alloc gains");
+  VK_A(d_part, (size_t)n_rows * n_tchunk * n_f, "alloc partial sums");
+  VK_A(d_phasor, (size_t)n_pol * seg.n_bl * n_f, "alloc phasor");
+  VK_A(d_gain, (size_t)n_pol * seg.n_bl * n_f, "alloc gains");
+  if (use_autos) VK_A(d_blst, (size_t)seg.n_bl, "alloc station pairs");
   VK_A(d_shifts, (size_t)prm.n_dm * n_f, "alloc shifts");
   VK_A(d_nvalid, (size_t)prm.n_dm, "alloc nvalid");
   VK_A(d_tw_n, (size_t)n_f, "alloc twiddles");
@@ -251,24 +281,45 @@ int SegJob::alloc(cudaStream_t s, bool ordered) {
   return 0;
 }
 
-int SegJob::stage_input(cudaStream_t s) {
-  if (empty) return 0;
-  const size_t vis_n = (size_t)seg.n_bl * seg.n_ap * n_f;
+bool is_device_pointer(const void* p) {
   cudaPointerAttributes attr{};
-  if (cudaPointerGetAttributes(&attr, seg.vis) != cudaSuccess) {
+  if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
     cudaGetLastError();
-    attr.type = cudaMemoryTypeUnregistered;
+    return false;
   }
-  if (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged) {
-    d_vis = static_cast<const float2*>(seg.vis);
+  return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+// Device pointer of a borrowed input: itself, or a stream-ordered copy of
+// host memory into *copy.
+static int stage_one(const void* src, size_t bytes, cudaStream_t s, bool ordered, void** copy, const void** dev,
+                     const char* what) {
+  if (is_device_pointer(src)) {
+    *dev = src;
     return 0;
   }
-  cudaError_t e = stream_ordered ? cudaMallocAsync(&d_vis_copy, vis_n * sizeof(float2), s)
-                                 : cudaMalloc(&d_vis_copy, vis_n * sizeof(float2));
-  if (e != cudaSuccess) return cuda_fail(e, "alloc vis copy");
-  e = cudaMemcpyAsync(d_vis_copy, seg.vis, vis_n * sizeof(float2), cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return cuda_fail(e, "copy vis to device");
-  d_vis = static_cast<const float2*>(d_vis_copy);
+  cudaError_t e = ordered ? cudaMallocAsync(copy, bytes, s) : cudaMalloc(copy, bytes);
+  if (e != cudaSuccess) return cuda_fail(e, what);
+  e = cudaMemcpyAsync(*copy, src, bytes, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(e, what);
+  *dev = *copy;
+  return 0;
+}
+
+int SegJob::stage_input(cudaStream_t s) {
+  if (empty) return 0;
+  const void* dv = nullptr;
+  int rc = stage_one(seg.vis, (size_t)n_pol * seg.n_bl * seg.n_ap * n_f * sizeof(float2), s, stream_ordered,
+                     &d_vis_copy, &dv, "copy vis to device");
+  if (rc) return rc;
+  d_vis = static_cast<const float2*>(dv);
+  if (use_autos) {
+    const void* da = nullptr;
+    rc = stage_one(seg.autos, (size_t)n_pol * seg.n_st * seg.n_ap * n_f * sizeof(float), s, stream_ordered,
+                   &d_autos_copy, &da, "copy auto spectra to device");
+    if (rc) return rc;
+    d_autos = static_cast<const float*>(da);
+  }
   return 0;
 }
 
@@ -280,6 +331,7 @@ int SegJob::upload(cudaStream_t s) {
                            cudaMemcpyHostToDevice, s)) != cudaSuccess)                        \
     return cuda_fail(e, what);
   VK_C(d_phasor, h_phasor, "copy phasor");
+  if (use_autos) VK_C(d_blst, h_blst, "copy station pairs");
   VK_C(d_shifts, shifts, "copy shifts");
   VK_C(d_nvalid, nvalid, "copy nvalid");
   VK_C(d_tw_n, h_tw_n, "copy twiddles");
@@ -289,14 +341,16 @@ int SegJob::upload(cudaStream_t s) {
 }
 
 void SegJob::release(cudaStream_t s) {
-  void* ptrs[] = {d_vis_copy, d_xn,   d_part,  d_phasor, d_gain, d_shifts, d_nvalid,
-                  d_tw_n,     d_tw_m, d_keys,  d_stats,  d_bits, d_cand,   d_count};
+  void* ptrs[] = {d_vis_copy, d_autos_copy, d_blst, d_xn,    d_part,  d_phasor, d_gain, d_shifts,
+                  d_nvalid,   d_tw_n,       d_tw_m, d_keys,  d_stats, d_bits,   d_cand, d_count};
   for (void* p : ptrs)
     if (p) {
       if (stream_ordered) cudaFreeAsync(p, s);
       else cudaFree(p);
     }
   d_vis_copy = nullptr;
+  d_autos_copy = nullptr;
+  d_blst = nullptr;
   d_xn = nullptr;
   d_part = nullptr;
   d_phasor = nullptr;
@@ -355,6 +409,10 @@ SegDesc SegJob::desc(int c) const {
 cudaError_t SegJob::enqueue_prep(cudaStream_t s, int* n_launch) const {
   PrepArgs pa{};
   pa.vis = d_vis;
+  pa.autos = use_autos ? d_autos : nullptr;
+  pa.bl_st = d_blst;
+  pa.n_pol = n_pol;
+  pa.n_st = seg.n_st;
   pa.xn = d_xn;
   pa.part = d_part;
   pa.phasor = d_phasor;
@@ -731,7 +789,7 @@ int volks_result_stats(volks_result* r, int32_t bl, int32_t dm_idx, int32_t win_
 int volks_result_gains(volks_result* r, float* gains, size_t cap_floats) {
   if (!r || !gains) return fail(VOLKS_EINVAL, "NULL argument");
   const vk::SegJob& j = *r->job;
-  const size_t n = (size_t)j.seg.n_bl * j.n_f * 2;
+  const size_t n = (size_t)j.n_pol * j.seg.n_bl * j.n_f * 2;
   if (cap_floats < n) return fail(VOLKS_EINVAL, "gains buffer holds %zu floats, need %zu", cap_floats, n);
   int rc = sync_result(r);
   if (rc) return rc;

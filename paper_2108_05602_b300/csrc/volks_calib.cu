@@ -129,8 +129,10 @@ extern "C" int volks_fringe_fit_calibrator(const volks_segment* seg, int32_t pad
   volks_default_params(&prm);
   int rc = vk::validate(seg, &prm);
   if (rc) return rc;
-  const int n_bl = seg->n_bl, n_ap = seg->n_ap, n_if = seg->n_if, J = seg->n_chan, n_f = n_if * J;
-  if (n_bl > 65535) return fail(VOLKS_EINVAL, "n_bl = %d: at most 65535 baselines per call", n_bl);
+  // the polarisation products are fitted independently: rows = (pol, baseline)
+  const int n_bl = (seg->n_pol == 2 ? 2 : 1) * seg->n_bl;
+  const int n_ap = seg->n_ap, n_if = seg->n_if, J = seg->n_chan, n_f = n_if * J;
+  if (n_bl > 65535) return fail(VOLKS_EINVAL, "n_pol * n_bl = %d: at most 65535 rows per call", n_bl);
   if ((long long)pad * J > 16384) return fail(VOLKS_EINVAL, "pad * n_chan = %lld cells: at most 16384", (long long)pad * J);
   const size_t n_out = (size_t)n_bl * n_if;
   if ((long long)n_bl * n_ap == 0) {

@@ -68,12 +68,16 @@ struct SearchVariant {
 };
 
 struct PrepArgs {
-  const float2* vis;               // [n_bl][n_ap][n_f]
-  float2* xn;                      // [n_bl][n_f][n_ap]  (normalised, calibrated)
-  double* part;                    // [n_bl][n_tchunk][n_f] partial sums of |S|^2
-  const double2* phasor;           // [n_bl][n_f] calibration phasor (FP64)
-  float2* gain;                    // [n_bl][n_f]
+  const float2* vis;               // [n_pol][n_bl][n_ap][n_f]
+  const float* autos;              // [n_pol][n_st][n_ap][n_f] auto-spectrum power, or NULL
+  const int2* bl_st;               // [n_bl] station pair of each baseline (with autos)
+  float2* xn;                      // [n_bl][n_f][n_ap]  (normalised, calibrated, polarisations summed)
+  double* part;                    // [n_rows][n_tchunk][n_f] partial sums of |S|^2 (rows = (pol, bl))
+                                   // or of a^2 (rows = (pol, station)) with autos
+  const double2* phasor;           // [n_pol][n_bl][n_f] calibration phasor (FP64)
+  float2* gain;                    // [n_pol][n_bl][n_f]
   int n_bl, n_ap, n_f, n_chan, n_tchunk, tchunk;
+  int n_pol, n_st;
   int normalize, skip_first_chan;
 };
 

@@ -17,26 +17,38 @@
 #include "../../include/volks.h"
 #include "fft_regs.cuh"
 #include "search_common.cuh"
+#include "search_kernel.cuh"
 #include "volks_internal.h"
 
 namespace vk {
 
 // ============================================================== prep ====
-// Partial sums of |S|^2 in FP64 over a chunk of APs, one thread per
-// (frequency point, AP phase); coalesced along frequency.
+// Partial sums in FP64 over a chunk of APs, one thread per (frequency
+// point, AP phase); coalesced along frequency.  Row r of the grid's z axis
+// is (polarisation, baseline) summing |S|^2 of the cross spectrum, or, with
+// auto spectra, (polarisation, station) summing a^2.
+template <bool AUTO>
 __global__ void __launch_bounds__(256) chan_power_kernel(const PrepArgs a) {
   __shared__ double red[8][33];
   const int k = blockIdx.x * 32 + threadIdx.x;
-  const int tc = blockIdx.y, b = blockIdx.z;
+  const int tc = blockIdx.y, row = blockIdx.z;
   const int t_beg = tc * a.tchunk;
   const int t_end = min(a.n_ap, t_beg + a.tchunk);
   double s = 0.0;
   if (k < a.n_f) {
-    const float2* v = a.vis + (size_t)b * a.n_ap * a.n_f + k;
-    for (int t = t_beg + (int)threadIdx.y; t < t_end; t += 8) {
-      const float2 x = v[(size_t)t * a.n_f];
-      s = fma((double)x.x, (double)x.x, s);
-      s = fma((double)x.y, (double)x.y, s);
+    if (AUTO) {
+      const float* v = a.autos + (size_t)row * a.n_ap * a.n_f + k;
+      for (int t = t_beg + (int)threadIdx.y; t < t_end; t += 8) {
+        const double x = (double)v[(size_t)t * a.n_f];
+        s = fma(x, x, s);
+      }
+    } else {
+      const float2* v = a.vis + (size_t)row * a.n_ap * a.n_f + k;
+      for (int t = t_beg + (int)threadIdx.y; t < t_end; t += 8) {
+        const float2 x = v[(size_t)t * a.n_f];
+        s = fma((double)x.x, (double)x.x, s);
+        s = fma((double)x.y, (double)x.y, s);
+      }
     }
   }
   red[threadIdx.y][threadIdx.x] = s;
@@ -45,45 +57,69 @@ __global__ void __launch_bounds__(256) chan_power_kernel(const PrepArgs a) {
     double t = 0.0;
 #pragma unroll
     for (int i = 0; i < 8; ++i) t += red[i][threadIdx.x];
-    a.part[((size_t)b * a.n_tchunk + tc) * a.n_f + k] = t;
+    a.part[((size_t)row * a.n_tchunk + tc) * a.n_f + k] = t;
   }
 }
 
-// gain = phasor / rms (FP64, then rounded once to FP32).
+__device__ __forceinline__ double mean_power(const PrepArgs& a, int row, int k) {
+  double s = 0.0;
+  for (int tc = 0; tc < a.n_tchunk; ++tc) s += a.part[((size_t)row * a.n_tchunk + tc) * a.n_f + k];
+  return s / (double)a.n_ap;
+}
+
+// gain[p][b][k] = phasor * normalisation (FP64, then rounded once to FP32):
+// 1 / RMS of the cross spectrum, or (mean a_i^2 mean a_j^2)^(-1/4) with the
+// stations' auto spectra (HOPS, Sec. 2.2).
 __global__ void gain_kernel(const PrepArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n_bl * a.n_f) return;
-  const int b = i / a.n_f, k = i % a.n_f;
-  double s = 0.0;
-  for (int tc = 0; tc < a.n_tchunk; ++tc) s += a.part[((size_t)b * a.n_tchunk + tc) * a.n_f + k];
+  if (i >= a.n_pol * a.n_bl * a.n_f) return;
+  const int pb = i / a.n_f, k = i % a.n_f;
   const double2 ph = a.phasor[i];
   double gr = ph.x, gi = ph.y;
   if (a.normalize) {
-    const double rms = sqrt(s / (double)a.n_ap);
-    if (rms > 0.0) {
-      gr /= rms;
-      gi /= rms;
+    double norm;
+    if (a.autos) {
+      const int p = pb / a.n_bl, b = pb % a.n_bl;
+      const int2 st = a.bl_st[b];
+      const double pij = mean_power(a, p * a.n_st + st.x, k) * mean_power(a, p * a.n_st + st.y, k);
+      norm = pij > 0.0 ? 1.0 / sqrt(sqrt(pij)) : 0.0;
     } else {
-      gr = gi = 0.0;
+      const double rms = sqrt(mean_power(a, pb, k));
+      norm = rms > 0.0 ? 1.0 / rms : 0.0;
     }
+    gr *= norm;
+    gi *= norm;
   }
   if (a.skip_first_chan && (k % a.n_chan) == 0) gr = gi = 0.0;
   a.gain[i] = make_float2((float)gr, (float)gi);
 }
 
-// xn[b][k][t] = vis[b][t][k] * gain[b][k]: 32x32 tiles through shared memory.
+// xn[b][k][t] = sum_p vis[p][b][t][k] * gain[p][b][k]: 32x32 tiles through
+// shared memory.
+template <int NPOL>
 __global__ void __launch_bounds__(256) normalize_transpose_kernel(const PrepArgs a) {
   __shared__ float2 tile[32][33];
   const int t0 = blockIdx.x * 32, k0 = blockIdx.y * 32, b = blockIdx.z;
   const int k = k0 + threadIdx.x;
-  const float2 g = a.gain[(size_t)b * a.n_f + k];
+  const size_t plane = (size_t)a.n_bl * a.n_ap * a.n_f;
+  float2 g[NPOL];
+#pragma unroll
+  for (int p = 0; p < NPOL; ++p) g[p] = a.gain[((size_t)p * a.n_bl + b) * a.n_f + k];
   const float2* v = a.vis + (size_t)b * a.n_ap * a.n_f;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int tl = threadIdx.y + 8 * i;
     const int t = t0 + tl;
     float2 x = make_float2(0.f, 0.f);
-    if (t < a.n_ap) x = cmul(v[(size_t)t * a.n_f + k], g);
+    if (t < a.n_ap) {
+      x = cmul(v[(size_t)t * a.n_f + k], g[0]);
+#pragma unroll
+      for (int p = 1; p < NPOL; ++p) {
+        const float2 y = cmul(v[p * plane + (size_t)t * a.n_f + k], g[p]);
+        x.x += y.x;
+        x.y += y.y;
+      }
+    }
     tile[tl][threadIdx.x] = x;
   }
   __syncthreads();
@@ -98,171 +134,34 @@ __global__ void __launch_bounds__(256) normalize_transpose_kernel(const PrepArgs
 
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s, int* n_launch) {
   dim3 blk(32, 8);
-  chan_power_kernel<<<dim3((a.n_f + 31) / 32, a.n_tchunk, a.n_bl), blk, 0, s>>>(a);
-  gain_kernel<<<(a.n_bl * a.n_f + 255) / 256, 256, 0, s>>>(a);
-  normalize_transpose_kernel<<<dim3((a.n_ap + 31) / 32, a.n_f / 32, a.n_bl), blk, 0, s>>>(a);
-  *n_launch += 3;
+  const bool autos = a.normalize && a.autos;
+  const int rows = a.n_pol * (autos ? a.n_st : a.n_bl);
+  if (a.normalize) {
+    if (autos)
+      chan_power_kernel<true><<<dim3((a.n_f + 31) / 32, a.n_tchunk, rows), blk, 0, s>>>(a);
+    else
+      chan_power_kernel<false><<<dim3((a.n_f + 31) / 32, a.n_tchunk, rows), blk, 0, s>>>(a);
+    *n_launch += 1;
+  }
+  gain_kernel<<<(a.n_pol * a.n_bl * a.n_f + 255) / 256, 256, 0, s>>>(a);
+  const dim3 grid((a.n_ap + 31) / 32, a.n_f / 32, a.n_bl);
+  if (a.n_pol == 2)
+    normalize_transpose_kernel<2><<<grid, blk, 0, s>>>(a);
+  else
+    normalize_transpose_kernel<1><<<grid, blk, 0, s>>>(a);
+  *n_launch += 2;
   return cudaGetLastError();
 }
 
 // ============================================================ search ====
-// Stage 3 of one unit on CUDA cores after the delay stage: thread = delay
-// column c, FP32 rate FFTs of every window, |Z|^2 and arg-max, merged over
-// the warps and published as one 64-bit atomicMax per segment.
-template <int N1, int PADR, int FOLD>
-__device__ __forceinline__ void search_tile(const UnitState& us, float2* S, uint2* slot) {
-  constexpr int N = 32 * N1;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  delay_stage<N1, FOLD>(us, S);
-  // ---- stage 3 ----
-  const int win_mask = us.a.win_mask;
-  // slot base of window 2^l: segments of the searched smaller windows first
-  auto slot_base = [&](int l) {
-    int o = 0;
-    for (int i = 0; i < l; ++i)
-      if (win_mask & (1 << i)) o += kTile >> i;
-    return o;
-  };
-  {
-    const int c = threadIdx.x;
-    const int P = us.a.pad_delay * FOLD;
-    const uint32_t m = (uint32_t)(c * P + us.r);
-    const uint32_t M = (uint32_t)us.a.M;
-    const int t0 = us.t0, nv = us.nv;
-    if (win_mask & 1) rate_window<1, PADR, N1>(S, c, m, M, t0, nv, slot_base(0), slot, warp, lane);
-    if (win_mask & 2) rate_window<2, PADR, N1>(S, c, m, M, t0, nv, slot_base(1), slot, warp, lane);
-    if (win_mask & 4) rate_window<4, PADR, N1>(S, c, m, M, t0, nv, slot_base(2), slot, warp, lane);
-    if (win_mask & 8) rate_window<8, PADR, N1>(S, c, m, M, t0, nv, slot_base(3), slot, warp, lane);
-    if (win_mask & 16) rate_window<16, PADR, N1>(S, c, m, M, t0, nv, slot_base(4), slot, warp, lane);
-    if (win_mask & 32) rate_window<32, PADR, N1>(S, c, m, M, t0, nv, slot_base(5), slot, warp, lane);
-  }
-  __syncthreads();
-  // ---- merge the warps' bests and publish one key per segment ----
-  const int ns = slot_base(kMaxWinLog + 1);
-  const int t0 = us.t0, nv = us.nv;
-  unsigned long long* keys =
-      us.a.keys + ((size_t)us.b * us.a.n_dm + us.d) * us.a.seg_per_bd;
-  for (int i = threadIdx.x; i < ns; i += N) {
-    int l = 0, base = 0;
-    for (;; ++l) {
-      if (!(win_mask & (1 << l))) continue;
-      if (i < base + (kTile >> l)) break;
-      base += kTile >> l;
-    }
-    const int s = i - base;
-    const int W = 1 << l;
-    const int sg = t0 / W + s;
-    if ((sg + 1) * W > nv) continue;
-    uint32_t bp = 0, bl = 0xffffffffu;
-#pragma unroll 4
-    for (int w = 0; w < N1; ++w) {
-      const uint2 e = slot[i * N1 + w];
-      if (e.x > bp || (e.x == bp && e.y < bl)) {
-        bp = e.x;
-        bl = e.y;
-      }
-    }
-    const unsigned long long key = ((unsigned long long)bp << 32) | (unsigned long long)(0xffffffffu - bl);
-    atomicMax(keys + us.a.win_off_l[l] + sg, key);
-  }
-}
+VK_MIXED_VARIANTS(VK_SEARCH_EXTERN, 0)
+VK_MIXED_VARIANTS(VK_SEARCH_EXTERN, 4)
 
-// Search kernel over the ranges of a Batch: one unit per CTA, or
-// persistent CTAs pulling units from an atomic counter (dynamic load
-// balancing across ranges of different sizes).
-template <int N1, int PADR, int FOLD>
-__global__ void __launch_bounds__(32 * N1, 16 / N1) search_kernel(const __grid_constant__ Batch p) {
-  constexpr int N = 32 * N1;
-  extern __shared__ __align__(16) float2 sm[];
-  float2* S = sm;
-  uint2* slot = reinterpret_cast<uint2*>(sm + 32 * (N + 1));
-  __shared__ UnitState us;
-  __shared__ int s_desc;
-  __shared__ long long s_unit;
-  const bool persistent = p.counter != nullptr;
-  long long next = (long long)blockIdx.x + p.unit0;
-  for (;;) {
-    if (threadIdx.x == 0) {
-      const long long u = persistent ? (long long)atomicAdd(p.counter, 1ULL) : next;
-      s_unit = u;
-      s_desc = u < p.total ? find_desc(p, u) : -1;
-    }
-    __syncthreads();
-    const int di = s_desc;
-    if (di < 0) return;
-    // copy the range descriptor to shared memory (8-byte words)
-    {
-      const unsigned long long* src = reinterpret_cast<const unsigned long long*>(&p.d[di]);
-      unsigned long long* dst = reinterpret_cast<unsigned long long*>(&us.a);
-      for (int i = threadIdx.x; i < (int)(sizeof(SegDesc) / 8); i += N) dst[i] = src[i];
-    }
-    if (threadIdx.x == 0) {
-      const SegDesc& a = p.d[di];
-      long long unit = s_unit - a.base;
-      const int P = a.pad_delay * FOLD;
-      us.r = (int)(unit % P);
-      unit /= P;
-      us.d = (int)(unit % a.n_dm);
-      unit /= a.n_dm;
-      const int tile = (int)(unit % a.n_tiles);
-      us.b = (int)(unit / a.n_tiles);
-      us.t0 = tile * kTile;
-      us.nv = a.nvalid[us.d];
-      us.valid = us.t0 < us.nv;
-    }
-    __syncthreads();
-    if (us.valid) search_tile<N1, PADR, FOLD>(us, S, slot);
-    if (!persistent) return;
-    __syncthreads();
-  }
-}
-
-template <int N1, int PADR, int FOLD>
-static size_t search_smem() {
-  return (size_t)32 * (32 * N1 + 1) * sizeof(float2) + (size_t)kMaxSegPerTile * N1 * sizeof(uint2);
-}
-
-template <int N1, int PADR, int FOLD>
-static cudaError_t launch_search_t(Batch& b, int grid_ctas, cudaStream_t s, int* n_launch) {
-  constexpr int N = 32 * N1;
-  const size_t smem = search_smem<N1, PADR, FOLD>();
-  cudaError_t e = cudaFuncSetAttribute(search_kernel<N1, PADR, FOLD>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  if (b.total <= 0) return cudaSuccess;
-  if (b.counter) {
-    b.unit0 = 0;
-    search_kernel<N1, PADR, FOLD><<<(unsigned)std::max(1, grid_ctas), N, smem, s>>>(b);
-    ++*n_launch;
-    return cudaGetLastError();
-  }
-  const long long max_grid = 2147483647LL;
-  for (long long u0 = 0; u0 < b.total; u0 += max_grid) {
-    b.unit0 = u0;
-    search_kernel<N1, PADR, FOLD><<<(unsigned)std::min(max_grid, b.total - u0), N, smem, s>>>(b);
-    ++*n_launch;
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
-}
-
-template <int N1, int PADR, int FOLD>
-static int occupancy_t() {
-  int n = 0;
-  if (cudaFuncSetAttribute(search_kernel<N1, PADR, FOLD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)search_smem<N1, PADR, FOLD>()) != cudaSuccess)
-    return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, search_kernel<N1, PADR, FOLD>, 32 * N1,
-                                                    search_smem<N1, PADR, FOLD>()) != cudaSuccess)
-    return 0;
-  return n;
-}
-
-// Compiled work splits: (n1, fold) with 32 * n1 * fold = n_f.
+// Compiled work splits: (n1, fold) with 32 * n1 * fold = n_f; n1 = 3, 6, 12
+// serve the bands of 3 * 2^a points (96 .. 1536) with mixed-radix FFTs.
 #define VK_VARIANTS(X, PADR)                                                           \
   X(2, PADR, 1) X(4, PADR, 1) X(8, PADR, 1) X(16, PADR, 1) X(8, PADR, 2) X(16, PADR, 2) \
-  X(8, PADR, 4) X(16, PADR, 4)
+  X(8, PADR, 4) X(16, PADR, 4) VK_MIXED_VARIANTS(X, PADR)
 
 int effective_precision(int n_f, int pad_rate, int precision) {
   if (precision == VOLKS_FP32 || pad_rate != 4) return VOLKS_FP32;

@@ -200,6 +200,8 @@ extern "C" int volks_search_peaks_noalloc(const volks_segment* seg, const volks_
   if (!(prm->pad_rate == 0 || prm->pad_rate == 4)) return na_fail(VOLKS_EINVAL, "pad_rate must be 0 or 4");
   if (prm->precision != VOLKS_FP32) return na_fail(VOLKS_EINVAL, "precision %d not available", prm->precision);
   if ((prm->normalize_chan & ~1) || (prm->skip_first_chan & ~1)) return na_fail(VOLKS_EINVAL, "flags must be 0 or 1");
+  if (seg->n_pol > 1 || seg->n_pol < 0 || seg->autos)
+    return na_fail(VOLKS_EINVAL, "this entry point takes one polarisation product and no auto spectra");
   if (seg->cal && (long long)n_bl * n_if > kMaxCal)
     return na_fail(VOLKS_EINVAL, "n_bl*n_if = %lld calibration entries; this entry point takes at most %d",
                    (long long)n_bl * n_if, kMaxCal);
@@ -305,6 +307,7 @@ extern "C" int volks_search_peaks_noalloc(const volks_segment* seg, const volks_
   pa.n_chan = n_chan;
   pa.n_tchunk = n_tchunk;
   pa.tchunk = tchunk;
+  pa.n_pol = 1;
   pa.normalize = prm->normalize_chan;
   pa.skip_first_chan = prm->skip_first_chan;
   if ((rc = cu(vk::launch_prep(pa, st, &n_launch), "prep kernels"))) return rc;

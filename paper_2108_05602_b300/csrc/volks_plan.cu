@@ -317,6 +317,8 @@ int volks_plan_create(const volks_segment* segs, const volks_params* prms, int32
         cudaGetLastError();
         return fail(VOLKS_EINVAL, "segment %d: a plan takes device-resident visibilities", i);
       }
+      if (segs[i].autos && prms[i].normalize_chan == 1 && !vk::is_device_pointer(segs[i].autos))
+        return fail(VOLKS_EINVAL, "segment %d: a plan takes device-resident auto spectra", i);
     }
   }
   volks_plan* p = new (std::nothrow) volks_plan();

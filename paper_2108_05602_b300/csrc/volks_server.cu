@@ -45,6 +45,7 @@ struct Request {
   volks_segment seg{};
   volks_params prm{};
   std::vector<double> cal;
+  std::vector<int32_t> bl_st;
   int64_t stream_id = -1;
   Clock::time_point t_submit, t_admit, t_done;
   int64_t bytes = 0;
@@ -115,6 +116,7 @@ int launch(volks_server* S, Request& r, Halo* h) {
   cudaStream_t st = S->streams[r.slot];
   volks_segment seg = r.seg;
   seg.cal = r.cal.empty() ? nullptr : r.cal.data();
+  seg.bl_st = r.bl_st.empty() ? nullptr : r.bl_st.data();
   if (S->cfg.fail_every > 0 && (S->admissions % S->cfg.fail_every) == 0)
     return fail(VOLKS_ENOMEM, "injected allocation failure (fail_every = %d)", S->cfg.fail_every);
   if (h) {
@@ -314,18 +316,20 @@ int volks_server_submit(volks_server* S, const volks_segment* seg, const volks_p
   r->seg = *seg;
   r->prm = *prm;
   r->stream_id = stream_id;
-  if (seg->cal) r->cal.assign(seg->cal, seg->cal + (size_t)seg->n_bl * seg->n_if * 2);
+  const size_t n_pol = seg->n_pol == 2 ? 2 : 1;
+  if (seg->cal) r->cal.assign(seg->cal, seg->cal + n_pol * seg->n_bl * seg->n_if * 2);
+  if (seg->autos && prm->normalize_chan == 1 && seg->bl_st)
+    r->bl_st.assign(seg->bl_st, seg->bl_st + (size_t)seg->n_bl * 2);
+  if (stream_id >= 0 && (n_pol > 1 || seg->autos))
+    return fail(VOLKS_EINVAL, "chained segments (stream_id >= 0) take one polarisation product and no auto spectra");
   // device bytes of the search (plus a copy of host input, plus the halo)
   vk::SegJob j;
   if ((rc = j.init(*seg, *prm, 0))) return rc;
   r->bytes = (int64_t)j.device_bytes();
-  cudaPointerAttributes attr{};
   const size_t vis_bytes = (size_t)seg->n_bl * seg->n_ap * j.n_f * sizeof(float2);
-  if (cudaPointerGetAttributes(&attr, seg->vis) != cudaSuccess ||
-      !(attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged)) {
-    cudaGetLastError();
-    r->bytes += (int64_t)vis_bytes;
-  }
+  if (!vk::is_device_pointer(seg->vis)) r->bytes += (int64_t)(n_pol * vis_bytes);
+  if (j.use_autos && !vk::is_device_pointer(seg->autos))
+    r->bytes += (int64_t)(j.input_bytes() - n_pol * vis_bytes);
   std::unique_lock<std::mutex> lk(S->mu);
   if (stream_id >= 0) {
     int H = 0;

@@ -222,6 +222,52 @@ def noise(wl: Workload, rng: np.random.Generator, n_ap: Optional[int] = None):
     return re.view(np.complex64)[..., 0]
 
 
+def station_pairs(n_bl: int):
+    """The smallest station count whose baselines cover n_bl, and the first
+    n_bl station pairs (i < j) in order: (n_st, bl_st int32 [n_bl][2])."""
+    n_st = 2
+    while n_st * (n_st - 1) // 2 < n_bl:
+        n_st += 1
+    pairs = [(i, j) for i in range(n_st) for j in range(i + 1, n_st)][:n_bl]
+    return n_st, np.array(pairs, dtype=np.int32).reshape(-1, 2)
+
+
+def bandpass(n_pol: int, n_st: int, n_f: int, rng: np.random.Generator) -> np.ndarray:
+    """Station power gain per polarisation and frequency point
+    [n_pol][n_st][n_f]: a level U[0.3, 3] times a smooth ripple of 1-4
+    cycles across the band, +-40 %."""
+    k = np.arange(n_f) / n_f
+    lvl = rng.uniform(0.3, 3.0, size=(n_pol, n_st, 1))
+    cyc = rng.uniform(1.0, 4.0, size=(n_pol, n_st, 1))
+    ph = rng.uniform(0.0, 2 * np.pi, size=(n_pol, n_st, 1))
+    return lvl * (1.0 + 0.4 * np.sin(2 * np.pi * cyc * k[None, None, :] + ph))
+
+
+def dual_pol_scan(wl: Workload, rng: np.random.Generator, pulses: List[Pulse], n_pol: int = 2,
+                  auto_jitter: float = 0.01, cal: Optional[np.ndarray] = None):
+    """A scan with n_pol polarisation products (e.g. LL, RR) seen through
+    the stations' bandpasses: product p of baseline (i, j) is
+    sqrt(g_pi g_pj) x (unit noise + the pulses with product p's instrumental
+    terms cal[p]); the stations' auto spectra are g_pi (1 + auto_jitter
+    N(0, 1)) per AP.  An unpolarised source: every product carries the same
+    pulses.  Returns (vis complex64 [n_pol][n_bl][n_ap][n_f], cal
+    [n_pol][n_bl][n_if][2], autos float32 [n_pol][n_st][n_ap][n_f], bl_st
+    [n_bl][2], g)."""
+    n_st, bl_st = station_pairs(wl.n_bl)
+    g = bandpass(n_pol, n_st, wl.n_f, rng)
+    if cal is None:
+        cal = np.stack([draw_calibration(wl, rng) for _ in range(n_pol)])
+    vis = np.empty((n_pol, wl.n_bl, wl.n_ap, wl.n_f), dtype=np.complex64)
+    for p in range(n_pol):
+        v = noise(wl, rng)
+        inject(v, wl, cal[p], pulses)
+        scale = np.sqrt(g[p, bl_st[:, 0]] * g[p, bl_st[:, 1]]).astype(np.float32)
+        vis[p] = v * scale[:, None, :]
+    jit = rng.standard_normal((n_pol, n_st, wl.n_ap, wl.n_f), dtype=np.float32)
+    autos = (g[:, :, None, :] * (1.0 + auto_jitter * jit)).astype(np.float32)
+    return vis, cal, autos, bl_st, g
+
+
 def pr1_pulse(wl: Workload, rng: np.random.Generator) -> Pulse:
     """The single PR1 pulse: DM 50, 2 ms (2 AP), SNR 10, 3.2 us, 0.5 Hz."""
     W = 2

@@ -25,7 +25,8 @@ class volks_segment(C.Structure):
     _fields_ = [("n_bl", C.c_int32), ("n_ap", C.c_int32), ("n_if", C.c_int32),
                 ("n_chan", C.c_int32), ("t_ap_s", C.c_double), ("f_lo_mhz", C.c_double),
                 ("chan_bw_mhz", C.c_double), ("vis", C.c_void_p),
-                ("cal", C.POINTER(C.c_double))]
+                ("cal", C.POINTER(C.c_double)), ("n_pol", C.c_int32), ("n_st", C.c_int32),
+                ("bl_st", C.POINTER(C.c_int32)), ("autos", C.c_void_p)]
 
 
 class volks_params(C.Structure):
@@ -229,16 +230,11 @@ def volks_search_peaks_noalloc(seg: volks_segment, prm: volks_params, stream: in
 def volks_fringe_fit_calibrator(wl, vis, pad: int = 4, stream: int = 0, n_bl=None, n_ap=None):
     """Initial calibration from a calibrator scan (see include/volks.h):
     returns (cal [n_bl][n_if][2] = (delay s, phase rad), amp [n_bl][n_if])."""
-    ptr, keep = _vis_pointer(vis)
     seg = volks_segment()
-    seg.n_bl = wl.n_bl if n_bl is None else n_bl
-    seg.n_ap = wl.n_ap if n_ap is None else n_ap
-    seg.n_if, seg.n_chan = wl.n_if, wl.n_chan
-    seg.t_ap_s, seg.f_lo_mhz, seg.chan_bw_mhz = wl.t_ap_s, wl.f_lo_mhz, wl.chan_bw_mhz
-    seg.vis = ptr
-    seg.cal = None
-    cal = np.zeros((seg.n_bl, wl.n_if, 2), dtype=np.float64)
-    amp = np.zeros((seg.n_bl, wl.n_if), dtype=np.float64)
+    keep = fill_segment(seg, wl, vis, None, None, None, n_bl, n_ap)
+    lead = (seg.n_pol,) if seg.n_pol == 2 else ()
+    cal = np.zeros(lead + (seg.n_bl, wl.n_if, 2), dtype=np.float64)
+    amp = np.zeros(lead + (seg.n_bl, wl.n_if), dtype=np.float64)
     DP = C.POINTER(C.c_double)
     _check(lib().volks_fringe_fit_calibrator(C.byref(seg), pad, C.c_void_p(stream),
                                              cal.ctypes.data_as(DP), amp.ctypes.data_as(DP)),
@@ -343,21 +339,54 @@ def _vis_pointer(vis):
     return arr.ctypes.data, arr
 
 
+def _autos_pointer(autos):
+    """(pointer, keepalive) of a contiguous float32 array or tensor."""
+    try:
+        import torch
+        if isinstance(autos, torch.Tensor):
+            if autos.dtype != torch.float32 or not autos.is_contiguous():
+                raise ValueError("autos must be a contiguous float32 tensor")
+            return autos.data_ptr(), autos
+    except ImportError:
+        pass
+    arr = np.ascontiguousarray(autos, dtype=np.float32)
+    return arr.ctypes.data, arr
+
+
+def fill_segment(seg: volks_segment, wl, vis, cal=None, autos=None, bl_st=None,
+                 n_bl: Optional[int] = None, n_ap: Optional[int] = None) -> list:
+    """Fill a segment descriptor; returns the objects that must outlive it.
+    vis [n_bl][n_ap][n_f] is one polarisation product, [n_pol][n_bl][n_ap][n_f]
+    two; cal [n_pol][n_bl][n_if][2] likewise; autos [n_pol][n_st][n_ap][n_f]
+    float32 with bl_st [n_bl][2] station indices, or None."""
+    ptr, keep_vis = _vis_pointer(vis)
+    seg.n_bl = wl.n_bl if n_bl is None else n_bl
+    seg.n_ap = wl.n_ap if n_ap is None else n_ap
+    seg.n_if, seg.n_chan = wl.n_if, wl.n_chan
+    seg.t_ap_s, seg.f_lo_mhz, seg.chan_bw_mhz = wl.t_ap_s, wl.f_lo_mhz, wl.chan_bw_mhz
+    seg.vis = ptr
+    seg.n_pol = int(vis.shape[0]) if len(vis.shape) == 4 else 1
+    calc = None if cal is None else np.ascontiguousarray(cal, dtype=np.float64)
+    seg.cal = None if calc is None else calc.ctypes.data_as(C.POINTER(C.c_double))
+    keep = [keep_vis, calc]
+    if autos is not None:
+        aptr, keep_a = _autos_pointer(autos)
+        st = np.ascontiguousarray(bl_st, dtype=np.int32)
+        seg.autos = aptr
+        seg.n_st = int(autos.shape[-3])
+        seg.bl_st = st.ctypes.data_as(C.POINTER(C.c_int32))
+        keep += [keep_a, st]
+    return keep
+
+
 class Search:
     """One search handle; frees its device scratch on close()/__del__."""
 
     def __init__(self, wl, vis, cal: Optional[np.ndarray] = None, stream: int = 0,
-                 n_bl: Optional[int] = None, n_ap: Optional[int] = None, **over):
-        ptr, self._keep_vis = _vis_pointer(vis)
-        self._cal = None if cal is None else np.ascontiguousarray(cal, dtype=np.float64)
+                 n_bl: Optional[int] = None, n_ap: Optional[int] = None, autos=None, bl_st=None,
+                 **over):
         seg = volks_segment()
-        seg.n_bl = wl.n_bl if n_bl is None else n_bl
-        seg.n_ap = wl.n_ap if n_ap is None else n_ap
-        seg.n_if, seg.n_chan = wl.n_if, wl.n_chan
-        seg.t_ap_s, seg.f_lo_mhz, seg.chan_bw_mhz = wl.t_ap_s, wl.f_lo_mhz, wl.chan_bw_mhz
-        seg.vis = ptr
-        seg.cal = (None if self._cal is None
-                   else self._cal.ctypes.data_as(C.POINTER(C.c_double)))
+        self._keep_vis = fill_segment(seg, wl, vis, cal, autos, bl_st, n_bl, n_ap)
         self.seg, self.prm = seg, make_params(wl, **over)
         self.n_f = wl.n_if * wl.n_chan
         self.n_bl = seg.n_bl
@@ -399,7 +428,10 @@ class Search:
         return mu.value, sd.value
 
     def gains(self) -> np.ndarray:
-        g = np.zeros((self.n_bl, self.n_f, 2), dtype=np.float32)
+        """[n_bl][n_f] complex gains, or [n_pol][n_bl][n_f] for two products."""
+        n_pol = self.seg.n_pol if getattr(self, "seg", None) is not None else 1
+        lead = (n_pol,) if n_pol == 2 else ()
+        g = np.zeros(lead + (self.n_bl, self.n_f, 2), dtype=np.float32)
         _check(lib().volks_result_gains(C.c_void_p(self.handle),
                                         g.ctypes.data_as(C.POINTER(C.c_float)), g.size), "gains")
         return g[..., 0] + 1j * g[..., 1]
@@ -428,19 +460,15 @@ class Plan:
         self._keep = []
         segs = (volks_segment * n)()
         prms = (volks_params * n)()
-        for i, (wl, vis, cal) in enumerate(items):
-            ptr, keep = _vis_pointer(vis)
-            calc = None if cal is None else np.ascontiguousarray(cal, dtype=np.float64)
-            self._keep += [keep, calc]
-            s = segs[i]
-            s.n_bl, s.n_ap, s.n_if, s.n_chan = wl.n_bl, wl.n_ap, wl.n_if, wl.n_chan
-            s.t_ap_s, s.f_lo_mhz, s.chan_bw_mhz = wl.t_ap_s, wl.f_lo_mhz, wl.chan_bw_mhz
-            s.vis = ptr
-            s.cal = None if calc is None else calc.ctypes.data_as(C.POINTER(C.c_double))
+        for i, item in enumerate(items):
+            wl, vis, cal = item[:3]
+            extra = item[3] if len(item) > 3 else {}
+            self._keep += fill_segment(segs[i], wl, vis, cal, extra.get("autos"), extra.get("bl_st"))
             prms[i] = make_params(wl, **over)
         self.n = n
-        self.n_f = [wl.n_if * wl.n_chan for wl, _, _ in items]
-        self.n_bl = [wl.n_bl for wl, _, _ in items]
+        self._segs = segs
+        self.n_f = [it[0].n_if * it[0].n_chan for it in items]
+        self.n_bl = [it[0].n_bl for it in items]
         self.prms = prms
         flags = (VOLKS_PLAN_AUTOTUNE if autotune else 0) | (VOLKS_PLAN_GRAPH if graph else 0)
         out = C.c_void_p()
@@ -466,7 +494,7 @@ class Plan:
                "volks_plan_result")
         r = Search.__new__(Search)
         r.handle, r.prm, r.n_f, r.borrowed = h.value, self.prms[i], self.n_f[i], True
-        r.seg, r.n_bl = None, self.n_bl[i]
+        r.seg, r.n_bl = self._segs[i], self.n_bl[i]
         return r
 
     def timing(self) -> volks_timing:
@@ -503,12 +531,9 @@ class Server:
         self.handle = out.value
         self._keep = {}
 
-    def submit(self, wl, vis, cal=None, stream_id: int = -1, **over) -> int:
-        ptr, keep = _vis_pointer(vis)
-        calc = None if cal is None else np.ascontiguousarray(cal, dtype=np.float64)
-        seg = volks_segment(wl.n_bl, wl.n_ap, wl.n_if, wl.n_chan, wl.t_ap_s, wl.f_lo_mhz,
-                            wl.chan_bw_mhz, ptr,
-                            None if calc is None else calc.ctypes.data_as(C.POINTER(C.c_double)))
+    def submit(self, wl, vis, cal=None, stream_id: int = -1, autos=None, bl_st=None, **over) -> int:
+        seg = volks_segment()
+        keep = fill_segment(seg, wl, vis, cal, autos, bl_st)
         prm = make_params(wl, **over)
         rid = C.c_uint64()
         _check(lib().volks_server_submit(C.c_void_p(self.handle), C.byref(seg), C.byref(prm),

@@ -90,6 +90,8 @@ def _seg(**kw):
     s.t_ap_s, s.f_lo_mhz, s.chan_bw_mhz = 1.024e-3, 1580.0, 0.5
     s.vis = 1  # never dereferenced: validation fails first
     for k, v in kw.items():
+        if k == "bl_st" and v is not None:
+            v = C.cast(v, C.POINTER(C.c_int32))
         setattr(s, k, v)
     return s
 
@@ -110,6 +112,12 @@ def _seg(**kw):
     ({}, dict(dm_lo=-10.0)),
     ({}, dict(min_windows=0)),
     ({}, dict(normalize_chan=2)),
+    (dict(n_pol=3), {}),
+    (dict(n_pol=-1), {}),
+    (dict(autos=1, n_st=1, bl_st=(C.c_int32 * 2)(0, 1)), {}),        # one station
+    (dict(autos=1, n_st=4, bl_st=None), {}),                           # no station pairs
+    (dict(autos=1, n_st=4, bl_st=(C.c_int32 * 2)(0, 4)), {}),        # station out of range
+    (dict(autos=1, n_st=4, bl_st=(C.c_int32 * 2)(2, 2)), {}),        # auto-correlation pair
 ])
 def test_malformed_descriptors_rejected(L, seg_kw, prm_kw):
     seg = _seg(**seg_kw)

@@ -74,8 +74,12 @@ def cell_power(Y, w, pad_rate, s, q, m):
     return abs(z) ** 2
 
 
-def check_peaks(wl, g, ref, vis, cal, normalize=True, skip_first_chan=False):
-    """Every segment of every (baseline, DM, window) series."""
+def check_peaks(wl, g, ref, vis, cal, normalize=True, skip_first_chan=False, autos=None, bl_st=None):
+    """Every segment of every (baseline, DM, window) series.  vis/cal may
+    carry a leading polarisation axis; autos/bl_st select the HOPS
+    normalisation."""
+    vis_pols = vis if vis.ndim == 4 else vis[None]
+    cal_pols = None if cal is None else (cal if np.ndim(cal) == 4 else np.asarray(cal)[None])
     n_checked = n_ties = 0
     Ycache = {}
     for (b, d, w), pk in ref.peaks.items():
@@ -91,8 +95,8 @@ def check_peaks(wl, g, ref, vis, cal, normalize=True, skip_first_chan=False):
         for s in bad:
             assert gap[s] < TIE_REL, ((b, d, w, s), (q[s], m[s]), (pk.q[s], pk.m[s]), gap[s])
             if (b, d) not in Ycache:
-                X = O.calibrate(vis[b], None if cal is None else cal[b], wl.n_if, wl.n_chan,
-                                wl.chan_bw_mhz, normalize, skip_first_chan)
+                X = O.prepare(vis_pols, cal_pols, b, wl.n_if, wl.n_chan, wl.chan_bw_mhz, normalize,
+                              skip_first_chan, autos, bl_st)
                 Ycache[(b, d)] = O.delay_transform(O.dedisperse(X, ref.shifts[d]), wl.pad_delay)
             pc = cell_power(Ycache[(b, d)], w, wl.pad_rate, s, q[s], m[s])
             assert pc >= (1 - TIE_REL) * pk.P[s]

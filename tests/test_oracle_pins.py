@@ -517,3 +517,84 @@ def test_localize_reports_collinear_partials():
     assert r.status == 0 and r.outlier == -1
     np.testing.assert_allclose(r.x, x_true, rtol=1e-9)
     assert np.isnan(r.loo[3]).all() and np.isfinite(r.loo[:3]).all()
+
+
+# ------------------------- polarisation combine, HOPS normalisation ----
+def test_auto_spectrum_normalisation_undoes_the_bandpass():
+    """Cross spectrum sqrt(g_i g_j) Z with constant auto spectra g: the
+    HOPS factor (mean a_i^2 mean a_j^2)^(-1/4) = 1/sqrt(g_i g_j) returns Z
+    (a square-root instead of a fourth root, or a_i instead of a_i^2,
+    leaves the bandpass in); a station without power zeroes its points."""
+    rng = np.random.default_rng(41)
+    n_ap, n_f = 50, 64
+    g = synth.bandpass(1, 3, n_f, rng)[0]
+    Z = rng.standard_normal((n_ap, n_f)) + 1j * rng.standard_normal((n_ap, n_f))
+    autos = np.broadcast_to(g[:, None, :], (3, n_ap, n_f))
+    i, j = 0, 2
+    S = Z * np.sqrt(g[i] * g[j])[None, :]
+    X = O.calibrate(S, None, 4, 16, 0.5, norm=O.auto_norm(autos[i], autos[j]))
+    np.testing.assert_allclose(X, Z, rtol=1e-12)
+    a0 = autos[i].copy()
+    a0[:, 5] = 0.0
+    f = O.auto_norm(a0, autos[j])
+    assert f[5] == 0.0 and np.all(f[np.arange(n_f) != 5] > 0)
+
+
+def test_polarisation_products_add_coherently_after_their_own_calibration():
+    """An on-grid pulse in two products with different instrumental terms:
+    each calibrated with its own table and summed, the peak is (2 a w N_f)^2
+    at the pulse's cell; calibrating each with the other's table loses
+    coherence."""
+    wl = synth.small(n_bl=1, n_ap=64, n_if=4, n_chan=16, n_dm=1)
+    rng = np.random.default_rng(42)
+    w, m0, q0 = 8, 37, 5
+    M, R = 4 * wl.n_f, 4 * w
+    cal = np.stack([synth.draw_calibration_on_grid(wl, rng) for _ in range(2)])
+    p = synth.Pulse(0.0, 3 * w, w, 6.0, np.array([m0 / (M * wl.chan_bw_mhz * 1e6)]),
+                    np.array([q0 / (R * wl.t_ap_s)]))
+    vis = np.zeros((2, 1, wl.n_ap, wl.n_f), dtype=np.complex128)
+    for pol in range(2):
+        rows, val = synth.pulse_footprint(wl, cal[pol], p)
+        for k in range(wl.n_f):
+            vis[pol, 0, rows[k], k] += val[0, k]
+    a = 6.0 * math.sqrt(2.0 / (w * wl.n_f))
+
+    def peak(c):
+        X = O.prepare(vis, c, 0, wl.n_if, wl.n_chan, wl.chan_bw_mhz, normalize=False)
+        Y = O.delay_transform(O.dedisperse(X, np.zeros(wl.n_f, dtype=np.int64)), 4)
+        pk = O.window_peaks(Y, w, 4)
+        return pk, 3
+
+    pk, s = peak(cal)
+    assert (int(pk.q[s]), int(pk.m[s])) == (q0, m0)
+    assert math.isclose(pk.P[s], (2 * a * w * wl.n_f) ** 2, rel_tol=1e-9)
+    pk_bad, _ = peak(cal[::-1])
+    assert pk_bad.P[s] < 0.9 * pk.P[s]
+
+
+def test_one_product_in_the_four_dimensional_layout_is_the_plain_search():
+    wl = synth.small(n_bl=2, n_ap=96, n_if=4, n_chan=16, n_dm=3, dm_step=20.0)
+    rng = np.random.default_rng(43)
+    vis = synth.noise(wl, rng)
+    cal = synth.draw_calibration(wl, rng)
+    a = O.search(wl, vis, cal)
+    b = O.search(wl, vis[None], cal[None])
+    for key in a.peaks:
+        np.testing.assert_array_equal(a.peaks[key].P, b.peaks[key].P)
+
+
+def test_two_normalised_noise_products_double_the_cell_power():
+    """Independent noise in two products adds incoherently: with the RMS
+    normalisation each product has unit power per point, so a delay cell's
+    mean power is 2 N_f; the HOPS normalisation removes the bandpass exactly
+    (no auto-spectrum jitter) and leaves the generator's variance of 2 per
+    point and product, so 4 N_f."""
+    wl = synth.small(n_bl=3, n_ap=400, n_if=4, n_chan=16)
+    rng = np.random.default_rng(44)
+    vis, cal, autos, bl_st, g = synth.dual_pol_scan(wl, rng, [], auto_jitter=0.0)
+    for kw in (dict(), dict(autos=autos, bl_st=bl_st)):
+        X = O.prepare(vis, cal, 1, wl.n_if, wl.n_chan, wl.chan_bw_mhz, **kw)
+        Y = O.delay_transform(X, 4)
+        mean = np.mean(np.abs(Y) ** 2) / wl.n_f
+        expect = 2.0 if not kw else 4.0
+        assert abs(mean / expect - 1) < 0.03, (kw.keys(), mean)
