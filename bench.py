@@ -50,6 +50,7 @@ WORKLOADS = {
 }
 # volks_params.precision of each workload (VOLKS_FP32 = 0, BF16 = 1, FP16 = 2, FP8 = 3)
 PRECISION = {"evn_bf16": 1, "evn_fp16": 2, "evn_fp8": 3, "evn_1bl_32dm_bf16": 1, "evn_1bl_32dm_fp8": 3}
+PREC_NAMES = {"fp32": 0, "bf16": 1, "fp16": 2, "fp8": 3}
 DTYPE = {0: "f32", 1: "bf16 rate GEMM + f32", 2: "f16 rate GEMM + f32", 3: "e4m3 rate GEMM + f32"}
 
 
@@ -265,6 +266,34 @@ def oracle_sample(wl, vis_b, cal_b, n_ap, dm_indices, cores):
     return n, dt
 
 
+def oracle_error_sample(wl, vis_t, cal, cands, n=16):
+    """Part of the CPU leg: the FP64 oracle's peak for the segments of the n
+    highest-z candidates, against the reported peak power and cell (error
+    of the reduced-precision search per candidate)."""
+    from oracle import volks_oracle as O
+    from paper_2108_05602_b300 import volks as V
+    sh, _ = V.volks_shift_table(wl.f_lo_mhz, wl.chan_bw_mhz, wl.n_f, wl.t_ap_s, wl.n_ap,
+                                wl.dm_lo, wl.dm_step, wl.n_dm)
+    top = sorted(cands, key=lambda c: -c["z"])[:n]
+    M = wl.pad_delay * wl.n_f
+    rel, same, Xc = [], 0, {}
+    for c in top:
+        b, d, w, sg = c["bl"], c["dm_idx"], c["win"], c["seg"]
+        if b not in Xc:
+            Xc[b] = O.calibrate(vis_t[b].cpu().numpy(), cal[b], wl.n_if, wl.n_chan, wl.chan_bw_mhz)
+        Xd = O.dedisperse(Xc[b], sh[d])[sg * w:(sg + 1) * w]
+        pk = O.window_peaks(O.delay_transform(Xd, wl.pad_delay), w, wl.pad_rate)
+        rel.append(abs(c["peak_power"] - pk.P[0]) / pk.P[0])
+        R = 1 if (w == 1 or wl.pad_rate == 0) else wl.pad_rate * w
+        q = c["rate_idx"] % R
+        m = c["delay_idx"] % M
+        same += int((q, m) == (int(pk.q[0]), int(pk.m[0])))
+    rel.sort()
+    return {"candidates": len(top), "max_rel_power_error": rel[-1] if rel else None,
+            "median_rel_power_error": rel[len(rel) // 2] if rel else None,
+            "peak_cell_equal": same, "sample": "the 16 highest-z candidates of the last step"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -419,6 +448,9 @@ def run_volks(args):
         achieved = flops / (ms_k / 1e3) / 1e12
         traffic = traffic_per_launch(args.workload)
         cpu = None
+        err = None
+        if not args.no_cpu_baseline and prec != 0:
+            err = oracle_error_sample(wl, vis, cal, cands, n=16)
         if not args.no_cpu_baseline:
             cores = min(8, os.cpu_count() or 1)
             n_ap = 9766  # 10 s of the scan
@@ -475,6 +507,8 @@ def run_volks(args):
         }
         if forms is not None:
             line["precision_forms"] = forms
+        if err is not None:
+            line["error_vs_oracle"] = err
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
@@ -530,8 +564,9 @@ def run_batch(args):
         return e0.elapsed_time(e1) / steps, res
 
     t_plain, r_plain = timed(plain_step, args.steps, args.warmup)
+    prec = PREC_NAMES[args.precision]
     t0 = time.perf_counter()
-    plan = V.Plan(items, autotune=True, graph=True)
+    plan = V.Plan(items, autotune=True, graph=True, precision=prec)
     create_s = time.perf_counter() - t0
 
     def plan_step():
@@ -550,7 +585,7 @@ def run_batch(args):
         "metric": METRIC.replace("EVN-scale scan", "64-segment heterogeneous batch"),
         "value": trials / (t_plan / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_plan, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[prec],
         "data": "synthetic: complex64 N(0,1) noise + 0-3 dispersed pulses per segment",
         "config": {"workload": "batch64", "segments": len(items),
                    "n_f": sorted({wl.n_f for wl in wls}),
@@ -565,10 +600,13 @@ def run_batch(args):
         "plain_fp32": {"value": trials / (t_plain / 1e3), "ms_per_step": t_plain,
                        "gpu_launches_per_step": 6 * len(items)},
         "speedup_vs_plain": t_plain / t_plan,
-        "roofline": {"bound": "alu", "kernel": "search_kernel (all band classes)",
+        "roofline": {"bound": "alu",
+                     "kernel": "search_kernel (all band classes)" if prec == 0 else
+                               "search_mma_kernel (n_f >= 256) + search_kernel (smaller bands)",
                      "achieved": flops / (ms_k / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
                      "frac": flops / (ms_k / 1e3) / 1e12 / peak, "traffic": None,
-                     "kernel_ms": ms_k, "algorithmic_flops": flops},
+                     "kernel_ms": ms_k, "algorithmic_flops": flops,
+                     "flops_basis": "nominal FFT-form flops of the search (same count for every precision)"},
         "gpu_launches": tm.n_launches,
         "clocks": clk.summary(),
         "candidates_per_step": r_plan[-1][0], "candidates_plain": r_plain[-1][0],
@@ -578,7 +616,7 @@ def run_batch(args):
     return 0
 
 
-def serve_once(V, srv, pool, rate_hz, duration_s, seed):
+def serve_once(V, srv, pool, rate_hz, duration_s, seed, prec=0):
     """Submit pool requests at Poisson times; return (completed trials,
     span s, p50 ms, p99 ms, peak inflight, n requests)."""
     arr = None
@@ -591,7 +629,7 @@ def serve_once(V, srv, pool, rate_hz, duration_s, seed):
         if dt > 0:
             time.sleep(dt)
         wl, vis, cal = pool[i % len(pool)]
-        ids.append(srv.submit(wl, vis, cal))
+        ids.append(srv.submit(wl, vis, cal, precision=prec))
     lat, trials = [], 0
     for rid in ids:
         info, _ = srv.wait(rid)
@@ -621,17 +659,18 @@ def run_serving(args):
         vis, cal, _ = synth.gen_segment_torch(wl, seed=2000 + i)
         pool.append((wl, vis, cal))
     torch.cuda.synchronize()
+    prec = PREC_NAMES[args.precision]
     srv = V.Server(max_inflight=8, hbm_budget_bytes=120 << 30)
     for wl, vis, cal in pool[: max(1, args.warmup)]:
-        srv.wait(srv.submit(wl, vis, cal))
+        srv.wait(srv.submit(wl, vis, cal, precision=prec))
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
-        trials, span, p50, p99, n = serve_once(V, srv, pool, 20.0, 30.0, seed=5)
+        trials, span, p50, p99, n = serve_once(V, srv, pool, 20.0, 30.0, seed=5, prec=prec)
     sweep = []
     slo_ms = 500.0
     rate, best = 20.0, (20.0 if p99 <= slo_ms else None)
     for _ in range(4):
         rate *= 1.25
-        tr, sp, a, b, m = serve_once(V, srv, pool, rate, 10.0, seed=int(rate))
+        tr, sp, a, b, m = serve_once(V, srv, pool, rate, 10.0, seed=int(rate), prec=prec)
         sweep.append({"rate_hz": rate, "p50_ms": a, "p99_ms": b, "trials_per_s": tr / sp, "requests": m})
         if b > slo_ms:
             break
@@ -642,7 +681,7 @@ def run_serving(args):
         "metric": "fringe-fit trials/sec under a Poisson request stream; p50/p99 latency",
         "value": trials / span, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": args.warmup,
         "ms_per_step": span * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32",
+        "vs_baseline": None, "dtype": DTYPE[prec],
         "data": "synthetic: 16 request shapes, complex64 noise + 0-3 pulses each",
         "config": {"workload": "serving", "rate_hz": 20.0, "duration_s": 30.0, "requests": n,
                    "max_inflight": 8, "hbm_budget_bytes": 120 << 30,
@@ -670,6 +709,8 @@ def main():
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the reduced-precision forms in the default EVN run")
     ap.add_argument("--workload", default="evn_fp32", choices=sorted(WORKLOADS) + ["batch64", "serving"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16", "fp8"],
+                    help="rate-search arithmetic of the batch64 plan and the serving requests")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
