@@ -99,6 +99,9 @@ def _seg(**kw):
 @pytest.mark.parametrize("seg_kw,prm_kw", [
     (dict(n_chan=15), {}),                       # n_f = 60 not a power of two
     (dict(n_if=64, n_chan=64), {}),              # n_f = 4096 not in this build
+    (dict(n_if=3, n_chan=16), {}),               # n_f = 48: 3 x 2^a below 96
+    (dict(n_if=12, n_chan=256), {}),             # n_f = 3072: 3 x 2^a above 1536
+    (dict(n_if=5, n_chan=64), {}),               # n_f = 320: factor 5
     (dict(n_ap=-1), {}),
     (dict(t_ap_s=0.0), {}),
     (dict(chan_bw_mhz=-0.5), {}),

@@ -136,12 +136,14 @@ def _tiny_segment(rng, W, n_if, n_chan):
     return rng.standard_normal((W, n_f)) + 1j * rng.standard_normal((W, n_f))
 
 
-def test_delay_transform_equals_eq1_brute_force():
+@pytest.mark.parametrize("n_if,n_chan", [(2, 8), (3, 8), (12, 8)])
+def test_delay_transform_equals_eq1_brute_force(n_if, n_chan):
     """Eq. 1 evaluated with physical frequencies (Hz) and delays (s) on every
     cell of the padded delay grid equals the oracle's FFT power, including
-    the calibration term that Eq. 1 carries inside Phi."""
+    the calibration term that Eq. 1 carries inside Phi; also for bands of
+    3 x 2^a points (12 IFs), which take mixed-radix transforms."""
     rng = np.random.default_rng(4)
-    n_if, n_chan, bw, f_lo = 2, 8, 0.5, 1600.0
+    bw, f_lo = 0.5, 1600.0
     S = _tiny_segment(rng, 1, n_if, n_chan)
     cal = np.stack([rng.uniform(-1e-7, 1e-7, n_if), rng.uniform(0, 6.28, n_if)], axis=1)
     M = 4 * n_if * n_chan
@@ -240,6 +242,27 @@ def test_on_grid_pulse_found_at_exact_cell(w, m0, q0):
     a = 6.0 * math.sqrt(2.0 / (w * wl.n_f))
     assert (int(pk.q[s]), int(pk.m[s])) == (q0 % R, m0 % M)
     assert math.isclose(pk.P[s], (a * w * wl.n_f) ** 2, rel_tol=1e-9)
+
+
+@pytest.mark.parametrize("n_if,n_chan", [(12, 16), (3, 32)])
+def test_on_grid_pulse_in_a_twelve_if_band(n_if, n_chan):
+    """Bands of 3 x 2^a points: an on-grid pulse peaks at its exact cell
+    with |Z| = a w N_f (M = 4 N_f is not a power of two)."""
+    wl = synth.small(n_bl=1, n_ap=64, n_if=n_if, n_chan=n_chan, n_dm=1)
+    w, m0, q0 = 8, -221, 6
+    M, R = 4 * wl.n_f, 4 * w
+    p = synth.Pulse(0.0, 2 * w, w, 6.0, np.array([m0 / (M * wl.chan_bw_mhz * 1e6)]),
+                    np.array([q0 / (R * wl.t_ap_s)]))
+    cal = np.zeros((1, wl.n_if, 2))
+    vis = np.zeros((1, wl.n_ap, wl.n_f), dtype=np.complex128)
+    rows, val = synth.pulse_footprint(wl, cal, p)
+    for k in range(wl.n_f):
+        vis[0, rows[k], k] += val[0, k]
+    X = O.calibrate(vis[0], cal[0], wl.n_if, wl.n_chan, wl.chan_bw_mhz, normalize=False)
+    pk = O.window_peaks(O.delay_transform(O.dedisperse(X, np.zeros(wl.n_f, dtype=np.int64)), 4), w, 4)
+    a = 6.0 * math.sqrt(2.0 / (w * wl.n_f))
+    assert (int(pk.q[2]), int(pk.m[2])) == (q0, m0 % M)
+    assert math.isclose(pk.P[2], (a * w * wl.n_f) ** 2, rel_tol=1e-9)
 
 
 def test_argmax_ties_go_to_lowest_linear_index():
