@@ -359,6 +359,17 @@ int volks_plan_info(volks_plan *plan, int32_t *n_rounds, int64_t *device_bytes,
                     int32_t *n_search_launches_per_run);
 void volks_plan_free(volks_plan *plan);
 
+/*
+ * One-shot batch search of n segments (the batching form of
+ * volks_search_segment): volks_plan_create with no peak budget, no
+ * autotuning and no graph, then one volks_plan_run on cuda_stream.
+ * Returns the plan in *out (free it with volks_plan_free); per-segment
+ * results come from volks_plan_result.  Same rules and errors as those two
+ * calls (visibilities and auto spectra in device memory).
+ */
+int volks_search_batch(const volks_segment *segs, const volks_params *prms, int32_t n,
+                       void *cuda_stream, volks_plan **out);
+
 /* ---- request server (continuous batching) --------------------------------
  *
  * volks_server_submit queues a scan segment and returns at once.  A

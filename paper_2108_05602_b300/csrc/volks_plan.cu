@@ -492,4 +492,20 @@ int volks_plan_info(volks_plan* p, int32_t* n_rounds, int64_t* device_bytes, int
 
 void volks_plan_free(volks_plan* p) { destroy(p); }
 
+int volks_search_batch(const volks_segment* segs, const volks_params* prms, int32_t n, void* cuda_stream,
+                       volks_plan** out) {
+  if (!out) return fail(VOLKS_EINVAL, "out is NULL");
+  *out = nullptr;
+  volks_plan* p = nullptr;
+  int rc = volks_plan_create(segs, prms, n, 0, 0, &p);
+  if (rc) return rc;
+  rc = volks_plan_run(p, nullptr, cuda_stream);
+  if (rc) {
+    volks_plan_free(p);
+    return rc;
+  }
+  *out = p;
+  return 0;
+}
+
 }  // extern "C"

@@ -169,6 +169,9 @@ def lib() -> C.CDLL:
     L.volks_fringe_fit_calibrator.restype = C.c_int
     L.volks_check_rate_gemm.argtypes = [P, I32, I32, I32, P]
     L.volks_check_rate_gemm.restype = C.c_int
+    L.volks_search_batch.argtypes = [C.POINTER(volks_segment), C.POINTER(volks_params), I32, P,
+                                     C.POINTER(P)]
+    L.volks_search_batch.restype = C.c_int
     L.volks_loc_default_params.argtypes = [C.POINTER(volks_loc_params)]
     L.volks_loc_default_params.restype = C.c_int
     L.volks_localize.argtypes = [C.POINTER(volks_loc_obs), I32, C.POINTER(volks_loc_params),
@@ -455,7 +458,9 @@ class Plan:
     overrides apply to every segment's parameters."""
 
     def __init__(self, items, peak_budget_bytes: int = 0, autotune: bool = True,
-                 graph: bool = True, **over):
+                 graph: bool = True, one_shot_stream: Optional[int] = None, **over):
+        """one_shot_stream: create and run at once through volks_search_batch
+        on that stream (no budget, autotuning or graph)."""
         n = len(items)
         self._keep = []
         segs = (volks_segment * n)()
@@ -472,8 +477,12 @@ class Plan:
         self.prms = prms
         flags = (VOLKS_PLAN_AUTOTUNE if autotune else 0) | (VOLKS_PLAN_GRAPH if graph else 0)
         out = C.c_void_p()
-        _check(lib().volks_plan_create(segs, prms, n, int(peak_budget_bytes), flags,
-                                       C.byref(out)), "volks_plan_create")
+        if one_shot_stream is not None:
+            _check(lib().volks_search_batch(segs, prms, n, C.c_void_p(one_shot_stream), C.byref(out)),
+                   "volks_search_batch")
+        else:
+            _check(lib().volks_plan_create(segs, prms, n, int(peak_budget_bytes), flags,
+                                           C.byref(out)), "volks_plan_create")
         self.handle = out.value
 
     def run(self, vis=None, stream: int = 0):

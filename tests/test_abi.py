@@ -151,6 +151,9 @@ def test_null_arguments(L):
     n = C.c_size_t()
     assert L.volks_candidates(None, None, 0, C.byref(n)) == V.VOLKS_EINVAL
     L.volks_free(None)  # NULL-safe
+    plan = C.c_void_p(123)
+    assert L.volks_search_batch(None, None, 0, None, C.byref(plan)) == V.VOLKS_EINVAL
+    assert plan.value is None
 
 
 def test_twiddle_series_matches_libm():

@@ -68,6 +68,17 @@ def test_plan_of_mixed_segments_matches_oracle(graph, autotune):
     plan.close()
 
 
+def test_one_shot_batch_matches_oracle():
+    """volks_search_batch: create + one run in a single call."""
+    items = _mixed()[:4]
+    dev = [torch.from_numpy(v).cuda() for _, v, _ in items]
+    plan = V.Plan([(wl, d, cal) for (wl, _, cal), d in zip(items, dev)],
+                  one_shot_stream=torch.cuda.current_stream().cuda_stream)
+    refs = [O.search(wl, vis, cal) for wl, vis, cal in items]
+    _check_all(plan, items, refs)
+    plan.close()
+
+
 def test_plan_dm_chunks_match_oracle():
     items = _mixed()[:3]
     dev = [torch.from_numpy(v).cuda() for _, v, _ in items]
