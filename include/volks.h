@@ -266,6 +266,27 @@ int volks_cross_match(const volks_candidate *in, size_t n, int32_t min_baselines
 int volks_fringe_fit_calibrator(const volks_segment *seg, int32_t pad, void *cuda_stream,
                                 double *cal_out, double *amp_out);
 
+/*
+ * Fine calibration (Sec. 2.1.2): the residual delay tau_cal of a reference
+ * source near the target, per baseline (and polarisation product), fitted
+ * with the target's scheme (Sec. 2.2), delay only -- the tau_cal of Eq. 2
+ * (volks_localize).  seg: the reference scan as for the search, with
+ * seg->cal the initial calibration.  Per row: each point normalised by its
+ * RMS over the scan and multiplied by the calibration phasor (steps a2,
+ * a3), integrated coherently over the scan in FP64, transformed to delay
+ * over all n_f points zero-padded by `pad` (one delay across the IFs, Eq.
+ * 1), and the largest |G| cell m* (lowest on ties, signed) gives
+ * tau_cal = m* / (pad n_f chan_bw), on the transform grid and ambiguous
+ * modulo 1 / chan_bw.
+ * tau_out: host, float64 [n_pol][n_bl].  amp_out: host, float64
+ * [n_pol][n_bl] = |G(m*)| / sum_k |S(k)|, or NULL.
+ * Runs on cuda_stream and waits for it.  Errors: VOLKS_EINVAL (sizes as
+ * for the search, pad 1/2/4/8, pad * n_f > 16384), VOLKS_ENOMEM,
+ * VOLKS_ECUDA.
+ */
+int volks_fine_calibration(const volks_segment *seg, int32_t pad, void *cuda_stream,
+                           double *tau_out, double *amp_out);
+
 /* ---- introspection, for checking each step against a reference ---- */
 
 /* Waits for the search.  Stage times and launch counts. */
@@ -437,6 +458,36 @@ int volks_server_get_stats(volks_server *srv, volks_server_stats *stats);
 int volks_server_drain(volks_server *srv, int32_t timeout_ms);
 /* Stops admitting, waits for running requests, frees everything. */
 void volks_server_free(volks_server *srv);
+
+/*
+ * Re-fit of detected pulses for localisation (Sec. 3.1.2: the pulse's
+ * visibilities are extracted and fitted again, and an SNR derived).  Per
+ * candidate (its bl, dm_idx, [t0_ap, t1_ap) and rate_hz, e.g. from
+ * volks_candidates of the same result): the search's normalised,
+ * calibrated, polarisation-combined visibilities of baseline bl,
+ * dedispersed at DM dm_idx, over APs t0_ap .. t1_ap - 1, summed coherently
+ * after removing the fringe rate, S(k) = sum_u X[t0 + u, k] exp(-2 pi i
+ * rate_hz u t_ap); delay transform over all n_f points zero-padded by pad
+ * (a power of two 1..32, pad * n_f <= 16384), peak cell m* (lowest on
+ * ties, signed), delay m* / (pad n_f chan_bw), SNR |G(m*)| / sqrt(W
+ * N_eff) (W = t1_ap - t0_ap; for unit-normalised noise a pulse of
+ * amplitude a per point gives a sqrt(W N_eff)), amplitude |G(m*)| /
+ * sum_k |S(k)|.  FP32 on the device; waits for the search first.
+ * res: a volks_search_segment or volks_plan_result handle (its data stay
+ * on the device until volks_free / volks_plan_free).  cands, out: host,
+ * n entries.  Errors: VOLKS_EINVAL (bad pad, a candidate outside the
+ * search's baselines, DMs or dedispersed APs, or longer than 1024 APs).
+ */
+typedef struct {
+  double delay_s;       /* delay of the peak on the pad * n_f grid */
+  double snr;           /* |G| / sqrt(W N_eff) */
+  double amp;           /* |G| / sum_k |S(k)| */
+  int32_t delay_idx;    /* signed cell, -pad n_f / 2 .. pad n_f / 2 - 1 */
+  int32_t n_ap;         /* W */
+} volks_refit;
+
+int volks_refit_pulses(volks_result *res, const volks_candidate *cands, int32_t n, int32_t pad,
+                       volks_refit *out);
 
 /*
  * Single-pulse localisation (Sec. 2.3, Eq. 2, with the rules of Sec.

@@ -27,6 +27,10 @@ and, around the search:
 
   initial calibration: fringe fit of a calibrator scan per baseline and IF
      (Sec. 2.1.1), giving the table a3 removes
+  fine calibration: residual band-wide delay of a reference source per
+     baseline (Sec. 2.1.2), the tau_cal of Eq. 2
+  pulse re-fit: the detected pulse's visibilities summed coherently and
+     fitted on a finer delay grid with its SNR (Sec. 3.1.2)
   localisation: least-squares position offset from the single pulse's
      delays (Sec. 2.3, Eq. 2) with the baseline cuts and the leave-one-out
      check of Sec. 3.1.2
@@ -184,6 +188,67 @@ def fringe_fit_calibrator(vis_b: np.ndarray, n_if: int, n_chan: int, chan_bw_mhz
         tot = np.abs(S).sum()
         amp[n] = abs(G[m]) / tot if tot > 0 else 0.0
     return CalFit(tau, phi, cell, amp)
+
+
+# --------------------------------------------------- fine calibration ----
+@dataclass
+class FineCal:
+    tau_s: float         # residual band-wide delay tau_cal
+    cell: int            # signed delay cell of the peak
+    amp: float           # |G(peak)| / sum_k |S(k)|
+
+
+def fine_calibration(vis_b: np.ndarray, cal_b: Optional[np.ndarray], n_if: int, n_chan: int,
+                     chan_bw_mhz: float, pad: int = 4) -> FineCal:
+    """Fine calibration (Sec. 2.1.2): the residual delay of a reference
+    source near the target, fitted per baseline with the target's scheme
+    (Sec. 2.2), delay only:
+
+      1. a2 + a3: per-point normalisation and the initial calibration;
+      2. coherent integration over the scan: S(k) = sum_t X[t, k];
+      3. one delay across all IFs: G(m) = sum_k S(k) exp(-2 pi i k m / (pad N_f));
+      4. peak m* (lowest on ties), signed: tau_cal = m* / (pad N_f chan_bw)."""
+    X = calibrate(vis_b, cal_b, n_if, n_chan, chan_bw_mhz, normalize=True)
+    S = X.sum(axis=0)
+    Mc = pad * n_if * n_chan
+    G = np.fft.fft(S, n=Mc)
+    m = int(np.argmax(G.real ** 2 + G.imag ** 2))
+    ms = m - Mc if m >= Mc // 2 else m
+    tot = np.abs(S).sum()
+    return FineCal(ms / (Mc * chan_bw_mhz * 1e6), ms, abs(G[m]) / tot if tot > 0 else 0.0)
+
+
+# ------------------------------------------------------ pulse re-fit ----
+@dataclass
+class Refit:
+    tau_s: float         # delay of the peak on the pad * N_f grid
+    cell: int            # signed cell
+    snr: float           # |G(peak)| / sqrt(W N_eff)
+    amp: float           # |G(peak)| / sum_k |S(k)|
+
+
+def refit_pulse(X: np.ndarray, shifts_row: np.ndarray, t0: int, t1: int, rate_hz: float, t_ap_s: float,
+                chan_bw_mhz: float, pad: int, n_eff: int) -> Refit:
+    """Re-fit of one detected pulse on one baseline for localisation (Sec.
+    3.1.2): the visibilities that hold the pulse (dedispersed APs t0..t1-1
+    of the normalised, calibrated X) are summed coherently after removing
+    the found fringe rate, S(k) = sum_u Xd[t0 + u, k] exp(-2 pi i rate u
+    T_AP), and fitted again on a finer delay grid, G(m) = sum_k S(k)
+    exp(-2 pi i k m / (pad N_f)); peak m* (lowest on ties), its delay, and
+    the SNR |G(m*)| / sqrt(W N_eff) of a coherent sum of W N_eff
+    unit-variance points."""
+    Xd = dedisperse(X, shifts_row)[t0:t1]
+    W = t1 - t0
+    u = np.arange(W)
+    S = (Xd * np.exp(-2j * np.pi * rate_hz * u * t_ap_s)[:, None]).sum(axis=0)
+    n_f = X.shape[1]
+    Mc = pad * n_f
+    G = np.fft.fft(S, n=Mc)
+    m = int(np.argmax(G.real ** 2 + G.imag ** 2))
+    ms = m - Mc if m >= Mc // 2 else m
+    tot = np.abs(S).sum()
+    return Refit(ms / (Mc * chan_bw_mhz * 1e6), ms, abs(G[m]) / math.sqrt(W * n_eff),
+                 abs(G[m]) / tot if tot > 0 else 0.0)
 
 
 # ------------------------------------------------------- localisation ----

@@ -476,6 +476,8 @@ int sync_result(volks_result* r) {
 
 }  // namespace
 
+int vk_sync_result(volks_result* r) { return sync_result(r); }
+
 int vk_rerun_match(volks_result* r) {
   vk::SegJob* j = r->job;
   cudaError_t e = cudaMemsetAsync(j->d_count, 0, sizeof(unsigned int), r->stream);

@@ -29,3 +29,6 @@ int vk_plan_timing(volks_plan* p, volks_timing* t);
 // Re-run the window match of a single-chunk job into its (regrown)
 // candidate buffer on r->stream.
 int vk_rerun_match(volks_result* r);
+
+// Wait for the result's stream and check the tensor-core error flag.
+int vk_sync_result(volks_result* r);

@@ -132,17 +132,22 @@ def draw_calibration(wl: Workload, rng: np.random.Generator) -> np.ndarray:
 
 
 def calibrator_scan(wl: Workload, cal: np.ndarray, amp: float, rng: Optional[np.random.Generator],
-                    n_ap: Optional[int] = None) -> np.ndarray:
-    """A strong continuum calibrator: every AP carries amp * exp(i (2 pi f_j
+                    n_ap: Optional[int] = None, tau_s: Optional[np.ndarray] = None) -> np.ndarray:
+    """A strong continuum source: every AP carries amp * exp(i (2 pi f_j
     dtau^n + dphi^n)) at channel j of IF n (f_j the channel-centre frequency
-    within the IF; (dtau, dphi) = cal[b, n]), plus unit noise when rng is
-    given.  complex64 [n_bl][n_ap][n_f]."""
+    within the IF; (dtau, dphi) = cal[b, n]), times exp(2 pi i f tau_s[b])
+    with f the frequency above the band's lower edge when a residual
+    band-wide delay is given (a reference source for fine calibration),
+    plus unit noise when rng is given.  complex64 [n_bl][n_ap][n_f]."""
     n_ap = wl.n_ap if n_ap is None else n_ap
     k = np.arange(wl.n_f)
     n = k // wl.n_chan
     j = k % wl.n_chan
     f_j_hz = (j + 0.5) * wl.chan_bw_mhz * 1e6
     ph = 2 * np.pi * f_j_hz[None, :] * cal[:, n, 0] + cal[:, n, 1]       # [n_bl][n_f]
+    if tau_s is not None:
+        f_rel_hz = (k + 0.5) * wl.chan_bw_mhz * 1e6
+        ph = ph + 2 * np.pi * f_rel_hz[None, :] * np.asarray(tau_s, dtype=np.float64)[:, None]
     sig = (amp * np.exp(1j * ph)).astype(np.complex64)
     vis = np.broadcast_to(sig[:, None, :], (wl.n_bl, n_ap, wl.n_f)).copy()
     if rng is not None:

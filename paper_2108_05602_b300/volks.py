@@ -76,6 +76,11 @@ class volks_server_stats(C.Structure):
                 ("trials", C.c_int64), ("trials_per_s", C.c_double)]
 
 
+class volks_refit(C.Structure):
+    _fields_ = [("delay_s", C.c_double), ("snr", C.c_double), ("amp", C.c_double),
+                ("delay_idx", C.c_int32), ("n_ap", C.c_int32)]
+
+
 class volks_loc_obs(C.Structure):
     _fields_ = [("tau_s", C.c_double), ("tau_cal_s", C.c_double), ("dtau_dalpha", C.c_double),
                 ("dtau_ddelta", C.c_double), ("snr", C.c_double), ("proj_len_m", C.c_double)]
@@ -167,11 +172,16 @@ def lib() -> C.CDLL:
     L.volks_fringe_fit_calibrator.argtypes = [C.POINTER(volks_segment), I32, P, C.POINTER(C.c_double),
                                               C.POINTER(C.c_double)]
     L.volks_fringe_fit_calibrator.restype = C.c_int
+    L.volks_fine_calibration.argtypes = [C.POINTER(volks_segment), I32, P, C.POINTER(C.c_double),
+                                         C.POINTER(C.c_double)]
+    L.volks_fine_calibration.restype = C.c_int
     L.volks_check_rate_gemm.argtypes = [P, I32, I32, I32, P]
     L.volks_check_rate_gemm.restype = C.c_int
     L.volks_search_batch.argtypes = [C.POINTER(volks_segment), C.POINTER(volks_params), I32, P,
                                      C.POINTER(P)]
     L.volks_search_batch.restype = C.c_int
+    L.volks_refit_pulses.argtypes = [P, C.POINTER(volks_candidate), I32, I32, C.POINTER(volks_refit)]
+    L.volks_refit_pulses.restype = C.c_int
     L.volks_loc_default_params.argtypes = [C.POINTER(volks_loc_params)]
     L.volks_loc_default_params.restype = C.c_int
     L.volks_localize.argtypes = [C.POINTER(volks_loc_obs), I32, C.POINTER(volks_loc_params),
@@ -244,6 +254,22 @@ def volks_fringe_fit_calibrator(wl, vis, pad: int = 4, stream: int = 0, n_bl=Non
            "volks_fringe_fit_calibrator")
     del keep
     return cal, amp
+
+
+def volks_fine_calibration(wl, vis, cal=None, pad: int = 4, stream: int = 0, n_ap=None):
+    """Residual band-wide delay of a reference scan per baseline (see
+    include/volks.h): returns (tau_cal [n_bl] s, amp [n_bl]), with a leading
+    polarisation axis for two products."""
+    seg = volks_segment()
+    keep = fill_segment(seg, wl, vis, cal, n_ap=n_ap)
+    lead = (seg.n_pol,) if seg.n_pol == 2 else ()
+    tau = np.zeros(lead + (seg.n_bl,), dtype=np.float64)
+    amp = np.zeros(lead + (seg.n_bl,), dtype=np.float64)
+    DP = C.POINTER(C.c_double)
+    _check(lib().volks_fine_calibration(C.byref(seg), pad, C.c_void_p(stream), tau.ctypes.data_as(DP),
+                                        amp.ctypes.data_as(DP)), "volks_fine_calibration")
+    del keep
+    return tau, amp
 
 
 VOLKS_CHECK_SKIP_MMA = 1
@@ -369,6 +395,9 @@ def fill_segment(seg: volks_segment, wl, vis, cal=None, autos=None, bl_st=None,
     seg.t_ap_s, seg.f_lo_mhz, seg.chan_bw_mhz = wl.t_ap_s, wl.f_lo_mhz, wl.chan_bw_mhz
     seg.vis = ptr
     seg.n_pol = int(vis.shape[0]) if len(vis.shape) == 4 else 1
+    if seg.n_bl * seg.n_ap > 0 and tuple(vis.shape[-3:]) != (seg.n_bl, seg.n_ap, wl.n_if * wl.n_chan):
+        raise ValueError(f"vis shape {tuple(vis.shape)} does not hold [n_bl={seg.n_bl}][n_ap={seg.n_ap}]"
+                         f"[n_f={wl.n_if * wl.n_chan}]")
     calc = None if cal is None else np.ascontiguousarray(cal, dtype=np.float64)
     seg.cal = None if calc is None else calc.ctypes.data_as(C.POINTER(C.c_double))
     keep = [keep_vis, calc]
@@ -402,6 +431,18 @@ class Search:
         t = volks_timing()
         _check(lib().volks_result_timing(C.c_void_p(self.handle), C.byref(t)), "timing")
         return t
+
+    def refit(self, cands: Sequence[dict], pad: int = 16) -> List[dict]:
+        """volks_refit_pulses on candidate dicts: delay_s, snr, amp, delay_idx, n_ap each."""
+        n = len(cands)
+        arr = (volks_candidate * max(1, n))()
+        names = [k for k, _ in volks_candidate._fields_ if k != "_pad"]
+        for i, c in enumerate(cands):
+            for k in names:
+                setattr(arr[i], k, c[k])
+        out = (volks_refit * max(1, n))()
+        _check(lib().volks_refit_pulses(C.c_void_p(self.handle), arr, n, pad, out), "volks_refit_pulses")
+        return [{k: getattr(out[i], k) for k, _ in volks_refit._fields_} for i in range(n)]
 
     def shifts(self):
         sh = np.zeros((self.prm.n_dm, self.n_f), dtype=np.int32)

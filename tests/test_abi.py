@@ -47,7 +47,7 @@ def test_struct_layout_matches_c(L):
     structs = {"volks_segment": V.volks_segment, "volks_params": V.volks_params,
                "volks_candidate": V.volks_candidate, "volks_timing": V.volks_timing,
                "volks_loc_obs": V.volks_loc_obs, "volks_loc_params": V.volks_loc_params,
-               "volks_loc_result": V.volks_loc_result}
+               "volks_loc_result": V.volks_loc_result, "volks_refit": V.volks_refit}
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', 'int main(void){']
     for sname, cls in structs.items():
         lines.append(f'printf("{sname} %zu\\n", sizeof({sname}));')

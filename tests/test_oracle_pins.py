@@ -621,3 +621,92 @@ def test_two_normalised_noise_products_double_the_cell_power():
         mean = np.mean(np.abs(Y) ** 2) / wl.n_f
         expect = 2.0 if not kw else 4.0
         assert abs(mean / expect - 1) < 0.03, (kw.keys(), mean)
+
+
+# ------------------------------------------------- fine calibration ----
+def test_fine_calibration_recovers_an_on_grid_band_delay_exactly():
+    """A reference source with a residual delay on the band-wide grid and
+    per-IF instrumental terms: with the initial calibration applied the
+    residual delay is recovered exactly with amplitude 1 (positive delay,
+    positive cell); without it the IFs add incoherently."""
+    wl = synth.small(n_bl=3, n_ap=40, n_if=8, n_chan=32)
+    rng = np.random.default_rng(51)
+    cal = synth.draw_calibration(wl, rng)
+    M = 4 * wl.n_f
+    cells = np.array([37, -410, 511])
+    tau = cells / (M * wl.chan_bw_mhz * 1e6)
+    vis = synth.calibrator_scan(wl, cal, 1.0, None, tau_s=tau)
+    for b in range(wl.n_bl):
+        f = O.fine_calibration(vis[b], cal[b], wl.n_if, wl.n_chan, wl.chan_bw_mhz)
+        assert f.cell == cells[b]
+        assert f.tau_s == cells[b] / (M * wl.chan_bw_mhz * 1e6)
+        assert math.isclose(f.amp, 1.0, rel_tol=1e-9)
+        g = O.fine_calibration(vis[b], None, wl.n_if, wl.n_chan, wl.chan_bw_mhz)
+        assert g.amp < 0.8
+
+
+def test_fine_calibration_error_within_half_a_cell_off_grid():
+    wl = synth.small(n_bl=4, n_ap=30, n_if=4, n_chan=32)
+    rng = np.random.default_rng(52)
+    cal = synth.draw_calibration(wl, rng)
+    M = 4 * wl.n_f
+    cell_s = 1.0 / (M * wl.chan_bw_mhz * 1e6)
+    tau = rng.uniform(-200, 200, size=wl.n_bl) * cell_s
+    vis = synth.calibrator_scan(wl, cal, 1.0, None, tau_s=tau)
+    for b in range(wl.n_bl):
+        f = O.fine_calibration(vis[b], cal[b], wl.n_if, wl.n_chan, wl.chan_bw_mhz)
+        assert abs(f.tau_s - tau[b]) <= 0.5 * cell_s + 1e-18
+
+
+# ----------------------------------------------------- pulse re-fit ----
+def _pulse_only(wl, p, cal=None):
+    cal = np.zeros((wl.n_bl, wl.n_if, 2)) if cal is None else cal
+    vis = np.zeros((wl.n_bl, wl.n_ap, wl.n_f), dtype=np.complex128)
+    rows, val = synth.pulse_footprint(wl, cal, p)
+    for b in range(wl.n_bl):
+        for k in range(wl.n_f):
+            vis[b, rows[k], k] += val[b, k]
+    return vis
+
+
+def test_refit_finds_a_fine_grid_delay_exactly_and_its_snr():
+    """A noise-free pulse with delay m0 on the 16-times padded grid (not on
+    the search's 4-times grid) and a rate on the window's grid: the re-fit
+    lands on m0 with |G| = a W N_f, SNR = a sqrt(W N_f), amplitude 1."""
+    wl = synth.small(n_bl=1, n_ap=96, n_if=4, n_chan=16, n_dm=1)
+    W, m0, q0 = 8, 157, 3
+    R = 4 * W
+    nu = q0 / (R * wl.t_ap_s)
+    p = synth.Pulse(0.0, 40, W, 6.0, np.array([m0 / (16 * wl.n_f * wl.chan_bw_mhz * 1e6)]), np.array([nu]))
+    vis = _pulse_only(wl, p)
+    X = O.calibrate(vis[0], None, wl.n_if, wl.n_chan, wl.chan_bw_mhz, normalize=False)
+    r = O.refit_pulse(X, np.zeros(wl.n_f, dtype=np.int64), 40, 40 + W, nu, wl.t_ap_s, wl.chan_bw_mhz, 16, wl.n_f)
+    a = 6.0 * math.sqrt(2.0 / (W * wl.n_f))
+    assert r.cell == m0
+    assert math.isclose(r.snr, a * math.sqrt(W * wl.n_f), rel_tol=1e-9)
+    assert math.isclose(r.amp, 1.0, rel_tol=1e-9)
+    # removing the rate with the wrong sign loses coherence
+    bad = O.refit_pulse(X, np.zeros(wl.n_f, dtype=np.int64), 40, 40 + W, -nu, wl.t_ap_s, wl.chan_bw_mhz, 16,
+                        wl.n_f)
+    assert bad.snr < 0.5 * r.snr
+
+
+def test_refit_snr_of_a_pulse_in_noise_matches_the_injected_snr():
+    """Unit-normalised noise plus pulses of SNR 20: the re-fit's SNR
+    estimate is sqrt(snr^2 + noise) ~ 20 on average."""
+    wl = synth.small(n_bl=8, n_ap=200, n_if=4, n_chan=32, n_dm=1)
+    rng = np.random.default_rng(61)
+    M16 = 16 * wl.n_f
+    snrs = []
+    for rep in range(3):
+        vis = synth.noise(wl, rng)
+        m0 = rng.integers(-M16 // 2, M16 // 2, size=wl.n_bl)
+        p = synth.Pulse(0.0, 60, 4, 20.0, m0 / (M16 * wl.chan_bw_mhz * 1e6), np.zeros(wl.n_bl))
+        synth.inject(vis, wl, np.zeros((wl.n_bl, wl.n_if, 2)), [p])
+        for b in range(wl.n_bl):
+            X = O.calibrate(vis[b], None, wl.n_if, wl.n_chan, wl.chan_bw_mhz)
+            r = O.refit_pulse(X, np.zeros(wl.n_f, dtype=np.int64), 60, 64, 0.0, wl.t_ap_s, wl.chan_bw_mhz, 16,
+                              wl.n_f)
+            assert abs(r.cell - m0[b]) <= 1
+            snrs.append(r.snr)
+    assert abs(np.mean(snrs) / 20.0 - 1) < 0.1
