@@ -125,6 +125,10 @@ typedef struct {
  *      with the segment's auto spectra, or, without them, divides each
  *      frequency point by its cross-spectrum RMS over the segment (FP64);
  *      0 leaves the amplitudes as they are.
+ * stride: 0 (default) places the segments of window w back to back, at
+ *      dedispersed APs s w; 1 slides them by one AP (segment s starts at AP
+ *      s: n_valid - w + 1 segments per series, w times the trials).  Sliding
+ *      searches run the FP32 search kernel whatever precision asks.
  * skip_first_chan: 1 drops channel 0 of every IF (Eq. 1's inner sum read
  *      literally as j = 1 .. J-1).
  */
@@ -139,6 +143,7 @@ typedef struct {
   int32_t min_windows, min_baselines;
   int32_t precision;
   int32_t normalize_chan, skip_first_chan;
+  int32_t stride;       /* segment stride: 0 = w (back to back), 1 = sliding */
 } volks_params;
 
 /*
@@ -178,7 +183,7 @@ typedef struct volks_result volks_result;   /* opaque, library-owned */
 
 /* Fill *p with the paper's defaults: DM 0, step 1, 1 trial; windows 2,4,8,16;
  * pad_delay 4; pad_rate 4; thresh 3; min_windows 2; min_baselines 5; FP32;
- * normalize_chan 1; skip_first_chan 0. */
+ * normalize_chan 1; skip_first_chan 0; stride 0. */
 void volks_default_params(volks_params *p);
 
 /*

@@ -42,6 +42,7 @@ notes): dispersion constant 4.148808e3 s MHz^2 pc^-1 cm^3 referenced to the
 top channel centre and rounded half-up; frequency points at channel centres;
 Eq. 1's inner sum taken over all channels; normalisation by the per-channel
 RMS over the segment; f_ref = lower band edge; segments of w APs at stride w;
+segments at stride w by default or sliding (stride 1) when asked;
 normalised power rho = P / (w * N_eff) thresholded as a z-score over the
 (baseline, DM, window) series; matching by interval overlap; the calibrator
 delay on the padded delay grid and its phase at the IF's first channel
@@ -355,15 +356,17 @@ class Peaks:
 
 
 def window_peaks(Y: np.ndarray, w: int, pad_rate: int,
-                 with_second: bool = True, chunk_bytes: int = 1 << 28) -> Peaks:
+                 with_second: bool = True, chunk_bytes: int = 1 << 28,
+                 stride: Optional[int] = None) -> Peaks:
     """a6+a7 for one window size: segments s cover dedispersed APs
-    [s*w, (s+1)*w); the FFTed APs of a segment are combined by a zero-padded
-    DFT along time (rate cell q is nu = q / (R * T_AP); q = 0 is the paper's
-    coherent sum), then the maximum |Z|^2 over (q, m) is found, ties going to
-    the lowest q*M + m."""
+    [s*stride, s*stride + w) (stride w: back to back; 1: sliding); the FFTed
+    APs of a segment are combined by a zero-padded DFT along time (rate cell
+    q is nu = q / (R * T_AP); q = 0 is the paper's coherent sum), then the
+    maximum |Z|^2 over (q, m) is found, ties going to the lowest q*M + m."""
     n_t, M = Y.shape
     R = rate_len(w, pad_rate)
-    n_seg = n_t // w
+    st = w if stride is None else stride
+    n_seg = (n_t - w) // st + 1 if n_t >= w else 0
     P = np.zeros(n_seg)
     q = np.zeros(n_seg, dtype=np.int64)
     m = np.zeros(n_seg, dtype=np.int64)
@@ -371,7 +374,10 @@ def window_peaks(Y: np.ndarray, w: int, pad_rate: int,
     per = max(1, chunk_bytes // (16 * R * M))
     for s0 in range(0, n_seg, per):
         s1 = min(n_seg, s0 + per)
-        Ys = Y[s0 * w:s1 * w].reshape(s1 - s0, w, M)
+        if st == w:
+            Ys = Y[s0 * w:s1 * w].reshape(s1 - s0, w, M)
+        else:
+            Ys = np.stack([Y[i * st:i * st + w] for i in range(s0, s1)])
         Z = np.fft.fft(Ys, n=R, axis=1) if R > 1 else Ys.sum(axis=1, keepdims=True)
         pw = (Z.real ** 2 + Z.imag ** 2).reshape(s1 - s0, R * M)
         idx = np.argmax(pw, axis=1)            # first (lowest) index on ties
@@ -411,14 +417,15 @@ class Member:
     P: float
     q: int
     m: int
+    stride: int = 0      # segment start = s * stride (0: stride w)
 
     @property
     def t0(self):
-        return self.s * self.w
+        return self.s * (self.stride or self.w)
 
     @property
     def t1(self):
-        return (self.s + 1) * self.w
+        return self.t0 + self.w
 
 
 def overlap_components(items: List, start, end) -> List[List]:
@@ -541,7 +548,8 @@ def search(wl, vis: np.ndarray, cal: Optional[np.ndarray], *,
             Y = delay_transform(Xd, wl.pad_delay)
             members = []
             for w in wl.windows:
-                pk = window_peaks(Y, w, wl.pad_rate, with_second)
+                st = getattr(wl, "stride", 0) or w
+                pk = window_peaks(Y, w, wl.pad_rate, with_second, stride=st)
                 rho = pk.P / (w * n_eff)
                 mu, sd = series_stats(rho)
                 z = zscores(rho, mu, sd)
@@ -549,7 +557,7 @@ def search(wl, vis: np.ndarray, cal: Optional[np.ndarray], *,
                 res.peaks[key], res.stats[key], res.rho[key], res.z[key] = pk, (mu, sd), rho, z
                 for s in np.nonzero(z >= wl.thresh)[0]:
                     members.append(Member(w, int(s), float(z[s]), float(pk.P[s]),
-                                          int(pk.q[s]), int(pk.m[s])))
+                                          int(pk.q[s]), int(pk.m[s]), st))
             for rep, nw, g0, g1 in window_match(members, wl.min_windows):
                 R = rate_len(rep.w, wl.pad_rate)
                 di, ri = signed(rep.m, M), signed(rep.q, R)

@@ -60,7 +60,7 @@ __device__ __forceinline__ void rate_window(const float2* __restrict__ S, int c,
   constexpr int N = 32 * N1, LD = N + 1;
   constexpr int NSEG = kTile / W;
   constexpr int R = (W == 1 || PADR == 0) ? 1 : PADR * W;
-  const int nseg = min(NSEG, max(0, nv / W - t0 / W));
+  const int nseg = min(NSEG, max(0, nv - t0) / W);
 #pragma unroll 1
   for (int s = 0; s < nseg; ++s) {
     const float2* col = S + (s * W) * LD + c;
@@ -123,6 +123,7 @@ __device__ __forceinline__ int find_desc(const Batch& p, long long u) {
 struct UnitState {
   SegDesc a;
   int b, d, r, t0, nv, valid;
+  int wmask;  // windows this unit searches (sliding: those wider than its AP phase)
 };
 
 // One work unit = (baseline b, DM trial d, 32-AP tile, delay residue r).

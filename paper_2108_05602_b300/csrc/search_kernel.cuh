@@ -25,7 +25,7 @@ __device__ __forceinline__ void search_tile(const UnitState& us, float2* S, uint
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   delay_stage<N1, FOLD>(us, S);
   // ---- stage 3 ----
-  const int win_mask = us.a.win_mask;
+  const int win_mask = us.wmask;
   // slot base of window 2^l: segments of the searched smaller windows first
   auto slot_base = [&](int l) {
     int o = 0;
@@ -61,8 +61,9 @@ __device__ __forceinline__ void search_tile(const UnitState& us, float2* S, uint
     }
     const int s = i - base;
     const int W = 1 << l;
-    const int sg = t0 / W + s;
-    if ((sg + 1) * W > nv) continue;
+    const int start = t0 + s * W;
+    if (start + W > nv) continue;
+    const int sg = us.a.slide ? start : start >> l;
     uint32_t bp = 0, bl = 0xffffffffu;
 #pragma unroll 4
     for (int w = 0; w < N1; ++w) {
@@ -112,13 +113,22 @@ __global__ void __launch_bounds__(32 * N1, 16 / N1) search_kernel(const __grid_c
       const int P = a.pad_delay * FOLD;
       us.r = (int)(unit % P);
       unit /= P;
+      // sliding segments: a search of every window w back to back from AP
+      // phase phi < w, for each phase (the unit searches the windows wider
+      // than its phase)
+      int phi = 0;
+      if (a.n_phase > 1) {
+        phi = (int)(unit % a.n_phase);
+        unit /= a.n_phase;
+      }
       us.d = (int)(unit % a.n_dm);
       unit /= a.n_dm;
       const int tile = (int)(unit % a.n_tiles);
       us.b = (int)(unit / a.n_tiles);
-      us.t0 = tile * kTile;
+      us.t0 = phi + tile * kTile;
       us.nv = a.nvalid[us.d];
-      us.valid = us.t0 < us.nv;
+      us.wmask = phi > 0 ? a.win_mask & ~((1 << (32 - __clz(phi))) - 1) : a.win_mask;
+      us.valid = us.t0 < us.nv && us.wmask != 0;
     }
     __syncthreads();
     if (us.valid) search_tile<N1, PADR, FOLD>(us, S, slot);

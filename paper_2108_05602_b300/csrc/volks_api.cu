@@ -121,6 +121,7 @@ int validate(const volks_segment* s, const volks_params* p) {
   if (p->min_windows < 1 || p->min_baselines < 1)
     return fail(VOLKS_EINVAL, "min_windows and min_baselines must be >= 1");
   if ((p->normalize_chan & ~1) || (p->skip_first_chan & ~1)) return fail(VOLKS_EINVAL, "flags must be 0 or 1");
+  if (p->stride != 0 && p->stride != 1) return fail(VOLKS_EINVAL, "stride must be 0 (window) or 1 (sliding)");
   return 0;
 }
 
@@ -186,7 +187,8 @@ int SegJob::init(const volks_segment& s, const volks_params& p, int chunk) {
   n_eff = n_f - (p.skip_first_chan ? s.n_if : 0);
   n_tiles = (s.n_ap + kTile - 1) / kTile;
   n_tchunk = (s.n_ap + tchunk - 1) / tchunk;
-  prec = effective_precision(n_f, p.pad_rate, p.precision);
+  slide = p.stride == 1;
+  prec = slide ? VOLKS_FP32 : effective_precision(n_f, p.pad_rate, p.precision);
   win_mask = 0;
   long long so = 0, wo = 0;
   for (int l = 0; l <= kMaxWinLog; ++l) win_off_l[l] = 0;
@@ -195,7 +197,7 @@ int SegJob::init(const volks_segment& s, const volks_params& p, int chunk) {
     win_off[i] = (int)so;
     word_off[i] = (int)wo;
     win_off_l[win_log[i]] = (int)so;
-    const long long ns = s.n_ap / p.win[i];
+    const long long ns = seg_count(s.n_ap, win_log[i], slide ? 1 : 0);
     so += ns;
     wo += (ns + 31) / 32;
     win_mask |= 1 << win_log[i];
@@ -396,6 +398,8 @@ SegDesc SegJob::desc(int c) const {
   d.n_eff = n_eff;
   d.min_windows = prm.min_windows;
   d.win_mask = win_mask;
+  d.slide = slide ? 1 : 0;
+  d.n_phase = slide ? prm.win[prm.n_win - 1] : 1;
   for (int i = 0; i <= kMaxWinLog; ++i) {
     d.win_log[i] = win_log[i];
     d.win_off[i] = win_off[i];
@@ -517,6 +521,7 @@ void volks_default_params(volks_params* p) {
   p->precision = VOLKS_FP32;
   p->normalize_chan = 1;
   p->skip_first_chan = 0;
+  p->stride = 0;
 }
 
 int volks_search_segment(const volks_segment* seg, const volks_params* prm, void* cuda_stream,
@@ -654,7 +659,7 @@ int volks_candidates(volks_result* r, volks_candidate* buf, size_t cap, size_t* 
       o.dm_idx = c.dm_idx;
       o.win = W;
       o.seg = c.seg;
-      o.t0_ap = c.seg * W;
+      o.t0_ap = vk::seg_start(c.seg, c.win_log, j.slide ? 1 : 0);
       o.t1_ap = o.t0_ap + W;
       o.g0_ap = c.g0;
       o.g1_ap = c.g1;
@@ -748,7 +753,7 @@ int volks_result_peaks(volks_result* r, int32_t bl, int32_t dm_idx, int32_t win_
   int rc = sync_result(r);
   if (rc) return rc;
   const int W = 1 << j.win_log[win_idx];
-  const size_t ns = (size_t)std::max(0, j.nvalid[dm_idx]) / W;
+  const size_t ns = (size_t)vk::seg_count(j.nvalid[dm_idx], j.win_log[win_idx], j.slide ? 1 : 0);
   *n_seg = ns;
   const size_t n = std::min(ns, cap);
   if (n == 0 || j.empty) return 0;

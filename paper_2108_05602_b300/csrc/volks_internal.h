@@ -42,12 +42,22 @@ struct SegDesc {
   long long base;                  // first work unit of this range within its launch
   int n_bl, n_ap, n_f, n_dm, n_dm_total, d0, pad_delay, M, n_tiles;
   int n_win, n_eff, min_windows, win_mask;
+  int slide;                       // segments slide by one AP (else back to back)
+  int n_phase;                     // sliding: AP phases 0 .. n_phase - 1 of the search units (else 1)
   int win_log[kMaxWinLog + 1];     // by window index
   int win_off[kMaxWinLog + 1];     // segment offset, by window index
   int word_off[kMaxWinLog + 1];    // bit-word offset, by window index
   int win_off_l[kMaxWinLog + 1];   // segment offset, by log2(window)
   double thresh;
 };
+
+// Segments of window 2^l in a series of nv dedispersed APs, and the first
+// AP of segment s: back to back (stride 2^l) or sliding (stride 1).
+__host__ __device__ inline int seg_count(int nv, int l, int slide) {
+  nv = nv > 0 ? nv : 0;
+  return slide ? (nv >= (1 << l) ? nv - (1 << l) + 1 : 0) : nv >> l;
+}
+__host__ __device__ inline int seg_start(int s, int l, int slide) { return slide ? s : s << l; }
 
 // A launch over up to kMaxDesc ranges.  counter == nullptr: unit
 // blockIdx.x + unit0 per CTA (per thread for the match kernel); otherwise

@@ -31,6 +31,7 @@ struct SegJob {
   int n_f = 0, M = 0, n_eff = 0, n_tiles = 0, n_tchunk = 0, tchunk = 1024, win_mask = 0;
   int prec = 0;              // effective precision of the rate search (effective_precision)
   int n_pol = 1;             // polarisation products summed after calibration
+  bool slide = false;        // sliding segments (stride 1)
   bool use_autos = false;    // HOPS normalisation with the stations' auto spectra
   int n_rows = 0;            // rows of the partial power sums: (pol, bl) or (pol, station)
   int win_log[kMaxWinLog + 1] = {}, win_off[kMaxWinLog + 1] = {}, word_off[kMaxWinLog + 1] = {};

@@ -201,7 +201,7 @@ SearchVariant default_variant(int n_f, int precision, int fold_override) {
 }
 
 long long search_units(const SegDesc& d, SearchVariant v) {
-  return (long long)d.n_bl * d.n_tiles * d.n_dm * d.pad_delay * v.fold;
+  return (long long)d.n_bl * d.n_tiles * d.n_dm * d.pad_delay * v.fold * std::max(1, d.n_phase);
 }
 
 int search_occupancy(SearchVariant v, int pad_rate, int precision) {
@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(256) select_kernel(const __grid_constant__ Bat
   const int d = (int)(ls % a.n_dm);
   const int b = (int)(ls / a.n_dm);
   const int W = 1 << a.win_log[wi];
-  const int nseg = max(a.nvalid[d], 0) / W;
+  const int nseg = seg_count(a.nvalid[d], a.win_log[wi], a.slide);
   const int n_eff = a.n_eff;
   const size_t bd = (size_t)b * a.n_dm + d;
   const unsigned long long* k = a.keys + bd * a.seg_per_bd + a.win_off[wi];
@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(128) match_kernel(const __grid_constant__ Batc
     wlog[wi] = a.win_log[wi];
     woff[wi] = a.win_off[wi];
     wdoff[wi] = a.word_off[wi];
-    const int nseg = nv >> wlog[wi];
+    const int nseg = seg_count(nv, wlog[wi], a.slide);
     nwords[wi] = (nseg + 31) / 32;
     wordi[wi] = 0;
     cur[wi] = nwords[wi] > 0 ? bits[wdoff[wi]] : 0u;
@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(128) match_kernel(const __grid_constant__ Batc
       }
       if (cur[wi] != 0u) {
         const int sg = wordi[wi] * 32 + __ffs(cur[wi]) - 1;
-        const int st = sg << wlog[wi];
+        const int st = seg_start(sg, wlog[wi], a.slide);
         if (st < bstart) {
           bstart = st;
           bw = wi;

@@ -200,6 +200,7 @@ extern "C" int volks_search_peaks_noalloc(const volks_segment* seg, const volks_
   if (!(prm->pad_rate == 0 || prm->pad_rate == 4)) return na_fail(VOLKS_EINVAL, "pad_rate must be 0 or 4");
   if (prm->precision != VOLKS_FP32) return na_fail(VOLKS_EINVAL, "precision %d not available", prm->precision);
   if ((prm->normalize_chan & ~1) || (prm->skip_first_chan & ~1)) return na_fail(VOLKS_EINVAL, "flags must be 0 or 1");
+  if (prm->stride != 0) return na_fail(VOLKS_EINVAL, "this entry point searches back-to-back segments only");
   if (seg->n_pol > 1 || seg->n_pol < 0 || seg->autos)
     return na_fail(VOLKS_EINVAL, "this entry point takes one polarisation product and no auto spectra");
   if (seg->cal && (long long)n_bl * n_if > kMaxCal)

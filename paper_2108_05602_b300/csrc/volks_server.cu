@@ -72,7 +72,7 @@ long long trial_count(const vk::SegJob& j) {
   long long n = 0;
   for (int d = 0; d < j.prm.n_dm; ++d) {
     const int nv = std::max(0, j.nvalid[d]);
-    for (int i = 0; i < j.prm.n_win; ++i) n += nv / j.prm.win[i];
+    for (int i = 0; i < j.prm.n_win; ++i) n += vk::seg_count(nv, j.win_log[i], j.slide ? 1 : 0);
   }
   return n * j.seg.n_bl;
 }

@@ -67,6 +67,7 @@ class Workload:
     thresh: float = 3.0
     min_windows: int = 2
     min_baselines: int = 5
+    stride: int = 0          # segment stride: 0 = w (back to back), 1 = sliding
 
     @property
     def n_f(self) -> int:

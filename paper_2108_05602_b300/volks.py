@@ -35,7 +35,7 @@ class volks_params(C.Structure):
                 ("pad_rate", C.c_int32), ("thresh", C.c_double),
                 ("min_windows", C.c_int32), ("min_baselines", C.c_int32),
                 ("precision", C.c_int32), ("normalize_chan", C.c_int32),
-                ("skip_first_chan", C.c_int32)]
+                ("skip_first_chan", C.c_int32), ("stride", C.c_int32)]
 
 
 class volks_candidate(C.Structure):
@@ -349,6 +349,7 @@ def make_params(wl, **over) -> volks_params:
         p.win[i] = w
     p.pad_delay, p.pad_rate = wl.pad_delay, wl.pad_rate
     p.thresh, p.min_windows, p.min_baselines = wl.thresh, wl.min_windows, wl.min_baselines
+    p.stride = getattr(wl, "stride", 0)
     for k, v in over.items():
         setattr(p, k, v)
     return p

@@ -115,6 +115,8 @@ def _seg(**kw):
     ({}, dict(dm_lo=-10.0)),
     ({}, dict(min_windows=0)),
     ({}, dict(normalize_chan=2)),
+    ({}, dict(stride=2)),
+    ({}, dict(stride=-1)),
     (dict(n_pol=3), {}),
     (dict(n_pol=-1), {}),
     (dict(autos=1, n_st=1, bl_st=(C.c_int32 * 2)(0, 1)), {}),        # one station

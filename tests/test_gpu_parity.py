@@ -67,10 +67,10 @@ def gpu_search(wl, vis, cal, device_input=True, **over):
     return s
 
 
-def cell_power(Y, w, pad_rate, s, q, m):
+def cell_power(Y, w, pad_rate, s, q, m, stride=None):
     R = O.rate_len(w, pad_rate)
     u = np.arange(w)
-    z = np.sum(Y[s * w + u, m] * np.exp(-2j * np.pi * q * u / R))
+    z = np.sum(Y[s * (stride or w) + u, m] * np.exp(-2j * np.pi * q * u / R))
     return abs(z) ** 2
 
 
@@ -98,7 +98,7 @@ def check_peaks(wl, g, ref, vis, cal, normalize=True, skip_first_chan=False, aut
                 X = O.prepare(vis_pols, cal_pols, b, wl.n_if, wl.n_chan, wl.chan_bw_mhz, normalize,
                               skip_first_chan, autos, bl_st)
                 Ycache[(b, d)] = O.delay_transform(O.dedisperse(X, ref.shifts[d]), wl.pad_delay)
-            pc = cell_power(Ycache[(b, d)], w, wl.pad_rate, s, q[s], m[s])
+            pc = cell_power(Ycache[(b, d)], w, wl.pad_rate, s, q[s], m[s], getattr(wl, "stride", 0) or w)
             assert pc >= (1 - TIE_REL) * pk.P[s]
             n_ties += 1
         mu, sd = g.stats(b, d, wi)

@@ -710,3 +710,42 @@ def test_refit_snr_of_a_pulse_in_noise_matches_the_injected_snr():
             assert abs(r.cell - m0[b]) <= 1
             snrs.append(r.snr)
     assert abs(np.mean(snrs) / 20.0 - 1) < 0.1
+
+
+# --------------------------------------------- sliding windows (stride 1) ----
+def test_sliding_segments_are_phase_shifted_strided_segments():
+    """Segment s of a sliding (stride 1) search of window w is segment
+    (s - phi) / w of the back-to-back search of the series shifted by
+    phi = s mod w; stride w is the default search; n - w + 1 segments."""
+    rng = np.random.default_rng(71)
+    Y = rng.standard_normal((70, 48)) + 1j * rng.standard_normal((70, 48))
+    for w in (1, 2, 4, 8):
+        sl = O.window_peaks(Y, w, 4, stride=1)
+        assert len(sl.P) == 70 - w + 1
+        np.testing.assert_array_equal(O.window_peaks(Y, w, 4, stride=w).P, O.window_peaks(Y, w, 4).P)
+        for phi in range(w):
+            ref = O.window_peaks(Y[phi:], w, 4)
+            idx = np.arange(phi, len(sl.P), w)
+            np.testing.assert_array_equal(sl.P[idx], ref.P[:len(idx)])
+            np.testing.assert_array_equal(sl.q[idx], ref.q[:len(idx)])
+            np.testing.assert_array_equal(sl.m[idx], ref.m[:len(idx)])
+
+
+def test_sliding_window_finds_a_pulse_that_straddles_two_segments():
+    """A noise-free on-grid pulse of 4 APs starting at AP 6: the
+    back-to-back 4-AP segments [4, 8) and [8, 12) each hold half of it;
+    the sliding segment starting at 6 holds all of it, at (a w N_f)^2."""
+    wl = synth.small(n_bl=1, n_ap=40, n_if=4, n_chan=16, n_dm=1)
+    w, m0 = 4, 21
+    M = 4 * wl.n_f
+    p = synth.Pulse(0.0, 6, w, 6.0, np.array([m0 / (M * wl.chan_bw_mhz * 1e6)]), np.zeros(1))
+    vis = _pulse_only(wl, p)
+    X = O.calibrate(vis[0], None, wl.n_if, wl.n_chan, wl.chan_bw_mhz, normalize=False)
+    Y = O.delay_transform(X, 4)
+    a = 6.0 * math.sqrt(2.0 / (w * wl.n_f))
+    full = (a * w * wl.n_f) ** 2
+    sl = O.window_peaks(Y, w, 4, stride=1)
+    assert int(np.argmax(sl.P)) == 6 and math.isclose(sl.P[6], full, rel_tol=1e-9)
+    assert (int(sl.q[6]), int(sl.m[6])) == (0, m0)
+    bb = O.window_peaks(Y, w, 4)
+    assert bb.P.max() < 0.5 * full
