@@ -53,14 +53,16 @@ __device__ __forceinline__ void rate_cells_w2(float2 y0, float2 y1, float (&P)[8
 // Rate transform, |Z|^2 and arg-max of every window-W segment of the tile
 // for the delay column this thread owns.  Per segment the warp's best
 // (power, lowest linear cell) goes to slot[(slot0 + s) * N1 + warp].
-template <int W, int PADR, int N1>
+template <int W, int PADR, int N1, bool SLIDE = false>
 __device__ __forceinline__ void rate_window(const float2* __restrict__ S, int c, uint32_t m,
                                             uint32_t M, int t0, int nv, int slot0,
                                             uint2* slot, int warp, int lane) {
   constexpr int N = 32 * N1, LD = N + 1;
   constexpr int NSEG = kTile / W;
   constexpr int R = (W == 1 || PADR == 0) ? 1 : PADR * W;
-  const int nseg = min(NSEG, max(0, nv - t0) / W);
+  // the tile's segments that end within the nv valid APs (a sliding unit's
+  // t0 need not be a multiple of W)
+  const int nseg = SLIDE ? min(NSEG, max(0, nv - t0) / W) : min(NSEG, max(0, nv / W - t0 / W));
 #pragma unroll 1
   for (int s = 0; s < nseg; ++s) {
     const float2* col = S + (s * W) * LD + c;
@@ -123,7 +125,6 @@ __device__ __forceinline__ int find_desc(const Batch& p, long long u) {
 struct UnitState {
   SegDesc a;
   int b, d, r, t0, nv, valid;
-  int wmask;  // windows this unit searches (sliding: those wider than its AP phase)
 };
 
 // One work unit = (baseline b, DM trial d, 32-AP tile, delay residue r).

@@ -19,13 +19,22 @@ namespace vk {
 // Stage 3 of one unit on CUDA cores after the delay stage: thread = delay
 // column c, FP32 rate FFTs of every window, |Z|^2 and arg-max, merged over
 // the warps and published as one 64-bit atomicMax per segment.
-template <int N1, int PADR, int FOLD>
+// Windows searched by a sliding-form unit whose tile starts at AP t0 (phase
+// phi = t0 mod 32): those wider than phi.
+__device__ __forceinline__ int sliding_windows(int win_mask, int t0) {
+  const int phi = t0 & (kTile - 1);
+  const int w = win_mask & kWinBits;
+  return phi > 0 ? w & ~((1 << (32 - __clz(phi))) - 1) : w;
+}
+
+template <int N1, int PADR, int FOLD, bool SLIDE>
 __device__ __forceinline__ void search_tile(const UnitState& us, float2* S, uint2* slot) {
   constexpr int N = 32 * N1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   delay_stage<N1, FOLD>(us, S);
   // ---- stage 3 ----
-  const int win_mask = us.wmask;
+  // a sliding unit of AP phase phi = t0 mod 32 searches the windows wider than phi
+  const int win_mask = SLIDE ? sliding_windows(us.a.win_mask, us.t0) : us.a.win_mask;
   // slot base of window 2^l: segments of the searched smaller windows first
   auto slot_base = [&](int l) {
     int o = 0;
@@ -39,12 +48,12 @@ __device__ __forceinline__ void search_tile(const UnitState& us, float2* S, uint
     const uint32_t m = (uint32_t)(c * P + us.r);
     const uint32_t M = (uint32_t)us.a.M;
     const int t0 = us.t0, nv = us.nv;
-    if (win_mask & 1) rate_window<1, PADR, N1>(S, c, m, M, t0, nv, slot_base(0), slot, warp, lane);
-    if (win_mask & 2) rate_window<2, PADR, N1>(S, c, m, M, t0, nv, slot_base(1), slot, warp, lane);
-    if (win_mask & 4) rate_window<4, PADR, N1>(S, c, m, M, t0, nv, slot_base(2), slot, warp, lane);
-    if (win_mask & 8) rate_window<8, PADR, N1>(S, c, m, M, t0, nv, slot_base(3), slot, warp, lane);
-    if (win_mask & 16) rate_window<16, PADR, N1>(S, c, m, M, t0, nv, slot_base(4), slot, warp, lane);
-    if (win_mask & 32) rate_window<32, PADR, N1>(S, c, m, M, t0, nv, slot_base(5), slot, warp, lane);
+    if (win_mask & 1) rate_window<1, PADR, N1, SLIDE>(S, c, m, M, t0, nv, slot_base(0), slot, warp, lane);
+    if (win_mask & 2) rate_window<2, PADR, N1, SLIDE>(S, c, m, M, t0, nv, slot_base(1), slot, warp, lane);
+    if (win_mask & 4) rate_window<4, PADR, N1, SLIDE>(S, c, m, M, t0, nv, slot_base(2), slot, warp, lane);
+    if (win_mask & 8) rate_window<8, PADR, N1, SLIDE>(S, c, m, M, t0, nv, slot_base(3), slot, warp, lane);
+    if (win_mask & 16) rate_window<16, PADR, N1, SLIDE>(S, c, m, M, t0, nv, slot_base(4), slot, warp, lane);
+    if (win_mask & 32) rate_window<32, PADR, N1, SLIDE>(S, c, m, M, t0, nv, slot_base(5), slot, warp, lane);
   }
   __syncthreads();
   // ---- merge the warps' bests and publish one key per segment ----
@@ -61,9 +70,15 @@ __device__ __forceinline__ void search_tile(const UnitState& us, float2* S, uint
     }
     const int s = i - base;
     const int W = 1 << l;
-    const int start = t0 + s * W;
-    if (start + W > nv) continue;
-    const int sg = us.a.slide ? start : start >> l;
+    int sg;
+    if constexpr (SLIDE) {
+      const int start = t0 + s * W;
+      if (start + W > nv) continue;
+      sg = desc_slide(us.a.win_mask) ? start : start >> l;
+    } else {
+      sg = t0 / W + s;
+      if ((sg + 1) * W > nv) continue;
+    }
     uint32_t bp = 0, bl = 0xffffffffu;
 #pragma unroll 4
     for (int w = 0; w < N1; ++w) {
@@ -81,7 +96,7 @@ __device__ __forceinline__ void search_tile(const UnitState& us, float2* S, uint
 // Search kernel over the ranges of a Batch: one unit per CTA, or
 // persistent CTAs pulling units from an atomic counter (dynamic load
 // balancing across ranges of different sizes).
-template <int N1, int PADR, int FOLD>
+template <int N1, int PADR, int FOLD, bool SLIDE>
 __global__ void __launch_bounds__(32 * N1, 16 / N1) search_kernel(const __grid_constant__ Batch p) {
   constexpr int N = 32 * N1;
   extern __shared__ __align__(16) float2 sm[];
@@ -117,9 +132,9 @@ __global__ void __launch_bounds__(32 * N1, 16 / N1) search_kernel(const __grid_c
       // phase phi < w, for each phase (the unit searches the windows wider
       // than its phase)
       int phi = 0;
-      if (a.n_phase > 1) {
-        phi = (int)(unit % a.n_phase);
-        unit /= a.n_phase;
+      if (SLIDE && desc_phases(a.win_mask) > 1) {
+        phi = (int)(unit % desc_phases(a.win_mask));
+        unit /= desc_phases(a.win_mask);
       }
       us.d = (int)(unit % a.n_dm);
       unit /= a.n_dm;
@@ -127,11 +142,10 @@ __global__ void __launch_bounds__(32 * N1, 16 / N1) search_kernel(const __grid_c
       us.b = (int)(unit / a.n_tiles);
       us.t0 = phi + tile * kTile;
       us.nv = a.nvalid[us.d];
-      us.wmask = phi > 0 ? a.win_mask & ~((1 << (32 - __clz(phi))) - 1) : a.win_mask;
-      us.valid = us.t0 < us.nv && us.wmask != 0;
+      us.valid = us.t0 < us.nv && (!SLIDE || sliding_windows(a.win_mask, us.t0) != 0);
     }
     __syncthreads();
-    if (us.valid) search_tile<N1, PADR, FOLD>(us, S, slot);
+    if (us.valid) search_tile<N1, PADR, FOLD, SLIDE>(us, S, slot);
     if (!persistent) return;
     __syncthreads();
   }
@@ -142,24 +156,24 @@ size_t search_smem() {
   return (size_t)32 * (32 * N1 + 1) * sizeof(float2) + (size_t)kMaxSegPerTile * N1 * sizeof(uint2);
 }
 
-template <int N1, int PADR, int FOLD>
+template <int N1, int PADR, int FOLD, bool SLIDE>
 cudaError_t launch_search_t(Batch& b, int grid_ctas, cudaStream_t s, int* n_launch) {
   constexpr int N = 32 * N1;
   const size_t smem = search_smem<N1, PADR, FOLD>();
-  cudaError_t e = cudaFuncSetAttribute(search_kernel<N1, PADR, FOLD>,
+  cudaError_t e = cudaFuncSetAttribute(search_kernel<N1, PADR, FOLD, SLIDE>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (b.total <= 0) return cudaSuccess;
   if (b.counter) {
     b.unit0 = 0;
-    search_kernel<N1, PADR, FOLD><<<(unsigned)std::max(1, grid_ctas), N, smem, s>>>(b);
+    search_kernel<N1, PADR, FOLD, SLIDE><<<(unsigned)std::max(1, grid_ctas), N, smem, s>>>(b);
     ++*n_launch;
     return cudaGetLastError();
   }
   const long long max_grid = 2147483647LL;
   for (long long u0 = 0; u0 < b.total; u0 += max_grid) {
     b.unit0 = u0;
-    search_kernel<N1, PADR, FOLD><<<(unsigned)std::min(max_grid, b.total - u0), N, smem, s>>>(b);
+    search_kernel<N1, PADR, FOLD, SLIDE><<<(unsigned)std::min(max_grid, b.total - u0), N, smem, s>>>(b);
     ++*n_launch;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -167,13 +181,13 @@ cudaError_t launch_search_t(Batch& b, int grid_ctas, cudaStream_t s, int* n_laun
   return cudaSuccess;
 }
 
-template <int N1, int PADR, int FOLD>
+template <int N1, int PADR, int FOLD, bool SLIDE>
 int occupancy_t() {
   int n = 0;
-  if (cudaFuncSetAttribute(search_kernel<N1, PADR, FOLD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (cudaFuncSetAttribute(search_kernel<N1, PADR, FOLD, SLIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)search_smem<N1, PADR, FOLD>()) != cudaSuccess)
     return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, search_kernel<N1, PADR, FOLD>, 32 * N1,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, search_kernel<N1, PADR, FOLD, SLIDE>, 32 * N1,
                                                     search_smem<N1, PADR, FOLD>()) != cudaSuccess)
     return 0;
   return n;
@@ -183,12 +197,22 @@ int occupancy_t() {
 // N1-point FFTs, instantiated in volks_search_mixed{0,4}.cu.
 #define VK_MIXED_VARIANTS(X, PADR) \
   X(3, PADR, 1) X(6, PADR, 1) X(12, PADR, 1) X(12, PADR, 2) X(12, PADR, 4)
+// Power-of-two work splits; their sliding forms are instantiated in
+// volks_search_slide{0,4}.cu.
+#define VK_POW2_VARIANTS(X, PADR)                                                      \
+  X(2, PADR, 1) X(4, PADR, 1) X(8, PADR, 1) X(16, PADR, 1) X(8, PADR, 2) X(16, PADR, 2) \
+  X(8, PADR, 4) X(16, PADR, 4)
 
-#define VK_SEARCH_INST(N1, PADR, FOLD)                                                   \
-  template cudaError_t launch_search_t<N1, PADR, FOLD>(Batch&, int, cudaStream_t, int*); \
-  template int occupancy_t<N1, PADR, FOLD>();
-#define VK_SEARCH_EXTERN(N1, PADR, FOLD)                                                        \
-  extern template cudaError_t launch_search_t<N1, PADR, FOLD>(Batch&, int, cudaStream_t, int*); \
-  extern template int occupancy_t<N1, PADR, FOLD>();
+#define VK_SEARCH_INST_S(N1, PADR, FOLD, SL)                                                \
+  template cudaError_t launch_search_t<N1, PADR, FOLD, SL>(Batch&, int, cudaStream_t, int*); \
+  template int occupancy_t<N1, PADR, FOLD, SL>();
+#define VK_SEARCH_EXTERN_S(N1, PADR, FOLD, SL)                                                     \
+  extern template cudaError_t launch_search_t<N1, PADR, FOLD, SL>(Batch&, int, cudaStream_t, int*); \
+  extern template int occupancy_t<N1, PADR, FOLD, SL>();
+#define VK_SEARCH_INST(N1, PADR, FOLD) VK_SEARCH_INST_S(N1, PADR, FOLD, false) VK_SEARCH_INST_S(N1, PADR, FOLD, true)
+#define VK_SEARCH_EXTERN(N1, PADR, FOLD) \
+  VK_SEARCH_EXTERN_S(N1, PADR, FOLD, false) VK_SEARCH_EXTERN_S(N1, PADR, FOLD, true)
+#define VK_SEARCH_INST_SLIDE(N1, PADR, FOLD) VK_SEARCH_INST_S(N1, PADR, FOLD, true)
+#define VK_SEARCH_EXTERN_SLIDE(N1, PADR, FOLD) VK_SEARCH_EXTERN_S(N1, PADR, FOLD, true)
 
 }  // namespace vk

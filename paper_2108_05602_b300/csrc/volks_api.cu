@@ -397,9 +397,7 @@ SegDesc SegJob::desc(int c) const {
   d.n_win = prm.n_win;
   d.n_eff = n_eff;
   d.min_windows = prm.min_windows;
-  d.win_mask = win_mask;
-  d.slide = slide ? 1 : 0;
-  d.n_phase = slide ? prm.win[prm.n_win - 1] : 1;
+  d.win_mask = win_mask | (slide ? kSlideBit | (prm.win[prm.n_win - 1] << 8) : 0);
   for (int i = 0; i <= kMaxWinLog; ++i) {
     d.win_log[i] = win_log[i];
     d.win_off[i] = win_off[i];

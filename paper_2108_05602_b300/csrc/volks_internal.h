@@ -42,8 +42,6 @@ struct SegDesc {
   long long base;                  // first work unit of this range within its launch
   int n_bl, n_ap, n_f, n_dm, n_dm_total, d0, pad_delay, M, n_tiles;
   int n_win, n_eff, min_windows, win_mask;
-  int slide;                       // segments slide by one AP (else back to back)
-  int n_phase;                     // sliding: AP phases 0 .. n_phase - 1 of the search units (else 1)
   int win_log[kMaxWinLog + 1];     // by window index
   int win_off[kMaxWinLog + 1];     // segment offset, by window index
   int word_off[kMaxWinLog + 1];    // bit-word offset, by window index
@@ -58,6 +56,18 @@ __host__ __device__ inline int seg_count(int nv, int l, int slide) {
   return slide ? (nv >= (1 << l) ? nv - (1 << l) + 1 : 0) : nv >> l;
 }
 __host__ __device__ inline int seg_start(int s, int l, int slide) { return slide ? s : s << l; }
+
+// SegDesc.win_mask: bits 0-5 the searched windows (bit l: 2^l APs); for
+// sliding segments bit 16 is set and bits 8-15 hold the number of AP phases
+// of the search units (the largest window).  Every window test reads the
+// low bits only.
+constexpr int kWinBits = 0x3f;
+constexpr int kSlideBit = 1 << 16;
+__host__ __device__ inline int desc_slide(int win_mask) { return (win_mask >> 16) & 1; }
+__host__ __device__ inline int desc_phases(int win_mask) {
+  const int n = (win_mask >> 8) & 0xff;
+  return n > 0 ? n : 1;
+}
 
 // A launch over up to kMaxDesc ranges.  counter == nullptr: unit
 // blockIdx.x + unit0 per CTA (per thread for the match kernel); otherwise

@@ -156,12 +156,12 @@ cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s, int* n_launch) {
 // ============================================================ search ====
 VK_MIXED_VARIANTS(VK_SEARCH_EXTERN, 0)
 VK_MIXED_VARIANTS(VK_SEARCH_EXTERN, 4)
+VK_POW2_VARIANTS(VK_SEARCH_EXTERN_SLIDE, 0)
+VK_POW2_VARIANTS(VK_SEARCH_EXTERN_SLIDE, 4)
 
 // Compiled work splits: (n1, fold) with 32 * n1 * fold = n_f; n1 = 3, 6, 12
 // serve the bands of 3 * 2^a points (96 .. 1536) with mixed-radix FFTs.
-#define VK_VARIANTS(X, PADR)                                                           \
-  X(2, PADR, 1) X(4, PADR, 1) X(8, PADR, 1) X(16, PADR, 1) X(8, PADR, 2) X(16, PADR, 2) \
-  X(8, PADR, 4) X(16, PADR, 4) VK_MIXED_VARIANTS(X, PADR)
+#define VK_VARIANTS(X, PADR) VK_POW2_VARIANTS(X, PADR) VK_MIXED_VARIANTS(X, PADR)
 
 int effective_precision(int n_f, int pad_rate, int precision) {
   if (precision == VOLKS_FP32 || pad_rate != 4) return VOLKS_FP32;
@@ -201,13 +201,13 @@ SearchVariant default_variant(int n_f, int precision, int fold_override) {
 }
 
 long long search_units(const SegDesc& d, SearchVariant v) {
-  return (long long)d.n_bl * d.n_tiles * d.n_dm * d.pad_delay * v.fold * std::max(1, d.n_phase);
+  return (long long)d.n_bl * d.n_tiles * d.n_dm * d.pad_delay * v.fold * desc_phases(d.win_mask);
 }
 
 int search_occupancy(SearchVariant v, int pad_rate, int precision) {
   if (precision != VOLKS_FP32) return mma_supported(v, pad_rate, precision) ? 1 : 0;
 #define VK_OCC(N1, PADR, FOLD) \
-  if (v.n1 == N1 && v.fold == FOLD && pad_rate == PADR) return occupancy_t<N1, PADR, FOLD>();
+  if (v.n1 == N1 && v.fold == FOLD && pad_rate == PADR) return occupancy_t<N1, PADR, FOLD, false>();
   VK_VARIANTS(VK_OCC, 0)
   VK_VARIANTS(VK_OCC, 4)
 #undef VK_OCC
@@ -220,9 +220,14 @@ cudaError_t launch_search_batch(Batch& b, SearchVariant v, int pad_rate, int pre
     if (!mma_supported(v, pad_rate, precision)) return cudaErrorInvalidValue;
     return launch_search_mma(b, v, precision, grid_ctas, s, n_launch);
   }
-#define VK_LAUNCH(N1, PADR, FOLD)                    \
-  if (v.n1 == N1 && v.fold == FOLD && pad_rate == PADR) \
-    return launch_search_t<N1, PADR, FOLD>(b, grid_ctas, s, n_launch);
+  // a launch with any sliding range takes the sliding form (which also
+  // serves back-to-back ranges)
+  bool slide = false;
+  for (int i = 0; i < b.n_desc; ++i) slide = slide || desc_slide(b.d[i].win_mask);
+#define VK_LAUNCH(N1, PADR, FOLD)                                                   \
+  if (v.n1 == N1 && v.fold == FOLD && pad_rate == PADR)                              \
+    return slide ? launch_search_t<N1, PADR, FOLD, true>(b, grid_ctas, s, n_launch) \
+                 : launch_search_t<N1, PADR, FOLD, false>(b, grid_ctas, s, n_launch);
   VK_VARIANTS(VK_LAUNCH, 0)
   VK_VARIANTS(VK_LAUNCH, 4)
 #undef VK_LAUNCH
@@ -295,7 +300,7 @@ __global__ void __launch_bounds__(256) select_kernel(const __grid_constant__ Bat
   const int d = (int)(ls % a.n_dm);
   const int b = (int)(ls / a.n_dm);
   const int W = 1 << a.win_log[wi];
-  const int nseg = seg_count(a.nvalid[d], a.win_log[wi], a.slide);
+  const int nseg = seg_count(a.nvalid[d], a.win_log[wi], desc_slide(a.win_mask));
   const int n_eff = a.n_eff;
   const size_t bd = (size_t)b * a.n_dm + d;
   const unsigned long long* k = a.keys + bd * a.seg_per_bd + a.win_off[wi];
@@ -357,7 +362,7 @@ __global__ void __launch_bounds__(128) match_kernel(const __grid_constant__ Batc
     wlog[wi] = a.win_log[wi];
     woff[wi] = a.win_off[wi];
     wdoff[wi] = a.word_off[wi];
-    const int nseg = seg_count(nv, wlog[wi], a.slide);
+    const int nseg = seg_count(nv, wlog[wi], desc_slide(a.win_mask));
     nwords[wi] = (nseg + 31) / 32;
     wordi[wi] = 0;
     cur[wi] = nwords[wi] > 0 ? bits[wdoff[wi]] : 0u;
@@ -397,7 +402,7 @@ __global__ void __launch_bounds__(128) match_kernel(const __grid_constant__ Batc
       }
       if (cur[wi] != 0u) {
         const int sg = wordi[wi] * 32 + __ffs(cur[wi]) - 1;
-        const int st = seg_start(sg, wlog[wi], a.slide);
+        const int st = seg_start(sg, wlog[wi], desc_slide(a.win_mask));
         if (st < bstart) {
           bstart = st;
           bw = wi;
