@@ -189,3 +189,21 @@ def test_product_path_does_not_touch_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"(from|import)\s+oracle\b|volks_oracle|oracle/", txt), f
+
+
+def test_binding_rejects_a_visibility_array_of_the_wrong_shape():
+    wl = synth.small(n_bl=2, n_ap=20, n_if=4, n_chan=16)
+    seg = V.volks_segment()
+    with pytest.raises(ValueError):
+        V.fill_segment(seg, wl, np.zeros((2, 21, wl.n_f), dtype=np.complex64))
+    keep = V.fill_segment(seg, wl, np.zeros((2, 2, 20, wl.n_f), dtype=np.complex64))
+    assert seg.n_pol == 2 and seg.n_bl == 2 and seg.n_ap == 20
+    del keep
+
+
+def test_default_params_include_the_stride():
+    p = V.volks_default_params()
+    assert p.stride == 0
+    wl = synth.small()
+    import dataclasses
+    assert V.make_params(dataclasses.replace(wl, stride=1)).stride == 1
