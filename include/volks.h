@@ -601,6 +601,14 @@ int volks_localize(const volks_loc_obs *obs, int32_t n, const volks_loc_params *
 int volks_search_peaks_noalloc(const volks_segment *seg, const volks_params *prm,
                                void *cuda_stream, float *peak_power, int32_t *peak_cell);
 
+/*
+ * Measured FP32 FMA throughput of the current device in TFLOP/s (2 flops
+ * per FMA): every SM runs 8 independent FMA chains per thread; timed with
+ * CUDA events on cuda_stream after one warm-up launch (~1 ms each).  The
+ * denominator of the FP32 search kernel's roofline, as a measurement.
+ */
+int volks_measure_fp32_peak(void *cuda_stream, double *tflops);
+
 #ifdef __cplusplus
 }
 #endif

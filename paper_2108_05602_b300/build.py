@@ -20,7 +20,7 @@ OBJ = os.path.join(HERE, "_build")
 SOURCES = ["volks_kernels.cu", "volks_mma.cu", "volks_api.cu", "volks_plan.cu", "volks_server.cu",
            "volks_noalloc.cu", "volks_calib.cu", "volks_loc.cpp",
            "volks_search_mixed0.cu", "volks_search_mixed4.cu", "volks_refit.cu",
-           "volks_search_slide0.cu", "volks_search_slide4.cu"]
+           "volks_search_slide0.cu", "volks_search_slide4.cu", "volks_probe.cu"]
 HEADERS = ["fft_regs.cuh", "twiddle_ce.h", "search_common.cuh", "search_kernel.cuh", "tcgen05.cuh", "volks_internal.h",
            "volks_job.h", "volks_result.h", os.path.join("..", "..", "include", "volks.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
