@@ -1,8 +1,10 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
 
-Tolerances (FP32 path; derivation in the design notes):
+Tolerances (FP32 path):
   * peak power and normalised power: relative 1e-4 (stated bound); the
-    FP32 transform error of a peak cell is ~1e-6 relative.
+    FP32 transform error of a peak cell is ~1e-6 relative (at most ~18
+    rounding stages of the delay and rate FFTs, the peak well above the
+    cell RMS), so the bound has a ~30x margin.
   * peak cell (q, m): identical, except where the oracle's best and
     second-best cells are within TIE_REL = 2e-5 relative of each other; there
     the GPU's cell must be one of those near-tied cells (oracle power at the
