@@ -37,12 +37,13 @@ and, around the search:
 
 Library primitives used as steps: numpy's FFT (a5, a6), argmax, sort.
 
-Readings of points the paper leaves open (each also listed in the design
-notes): dispersion constant 4.148808e3 s MHz^2 pc^-1 cm^3 referenced to the
-top channel centre and rounded half-up; frequency points at channel centres;
-Eq. 1's inner sum taken over all channels; normalisation by the per-channel
-RMS over the segment; f_ref = lower band edge; segments of w APs at stride w;
-segments at stride w by default or sliding (stride 1) when asked;
+Readings of points the paper leaves open: dispersion constant 4.148808e3
+s MHz^2 pc^-1 cm^3 referenced to the top channel centre and rounded
+half-up; frequency points at channel centres; Eq. 1's inner sum taken over
+all channels; normalisation by the HOPS auto-spectrum factor, or by the
+per-channel RMS over the segment without auto spectra; polarisation
+products summed after their own calibration; f_ref = lower band edge;
+segments of w APs at stride w by default, sliding (stride 1) when asked;
 normalised power rho = P / (w * N_eff) thresholded as a z-score over the
 (baseline, DM, window) series; matching by interval overlap; the calibrator
 delay on the padded delay grid and its phase at the IF's first channel
