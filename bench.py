@@ -144,8 +144,8 @@ def cuda_core_flops_mma(wl, nvalid) -> float:
 KERNEL_SOURCES = {
     # the FP32 search kernel and the tensor-core search kernel: sources whose
     # change invalidates a committed DRAM-traffic capture
-    "search_kernel_traffic.json": ("volks_kernels.cu", "search_kernel.cuh", "search_common.cuh", "fft_regs.cuh",
-                                   "twiddle_ce.h", "volks_internal.h"),
+    "search_kernel_traffic.json": ("search_kernel.cuh", "search_common.cuh", "fft_regs.cuh", "twiddle_ce.h",
+                                   "volks_internal.h"),
     "search_mma_kernel_traffic.json": ("volks_mma.cu", "tcgen05.cuh", "search_common.cuh", "fft_regs.cuh",
                                        "twiddle_ce.h", "volks_internal.h"),
 }

@@ -263,14 +263,19 @@ cudaError_t launch_search(const SearchArgs& a, int pad_rate, cudaStream_t s, int
 }
 
 // ============================================================ select ====
-// z-score of one segment, with round-to-nearest intrinsics so that the
-// select and match kernels compute bit-identical values.
-__device__ __forceinline__ double seg_rho(unsigned long long key, int W, int n_eff) {
+// Normalised power rho = P / (W N_eff) and z = (rho - mu) / sd of one
+// segment, each as a product with a reciprocal formed once per series (FP64
+// division is costly on this part), with round-to-nearest intrinsics so
+// that the select and match kernels compute bit-identical values.  sd = 0
+// (an all-equal series) gives inv_sd = 0 and so z = 0.
+__device__ __forceinline__ double seg_inv_wn(int W, int n_eff) { return __ddiv_rn(1.0, (double)(W * n_eff)); }
+__device__ __forceinline__ double seg_inv_sd(double sd) { return sd > 0.0 ? __ddiv_rn(1.0, sd) : 0.0; }
+__device__ __forceinline__ double seg_rho(unsigned long long key, double inv_wn) {
   const float P = __uint_as_float((uint32_t)(key >> 32));
-  return __ddiv_rn((double)P, (double)(W * n_eff));
+  return __dmul_rn((double)P, inv_wn);
 }
-__device__ __forceinline__ double seg_z(double rho, double mu, double sd) {
-  return sd > 0.0 ? __ddiv_rn(__dsub_rn(rho, mu), sd) : 0.0;
+__device__ __forceinline__ double seg_z(double rho, double mu, double inv_sd) {
+  return __dmul_rn(__dsub_rn(rho, mu), inv_sd);
 }
 
 template <int NT>
@@ -301,15 +306,15 @@ __global__ void __launch_bounds__(256) select_kernel(const __grid_constant__ Bat
   const int b = (int)(ls / a.n_dm);
   const int W = 1 << a.win_log[wi];
   const int nseg = seg_count(a.nvalid[d], a.win_log[wi], desc_slide(a.win_mask));
-  const int n_eff = a.n_eff;
+  const double inv_wn = seg_inv_wn(W, a.n_eff);
   const size_t bd = (size_t)b * a.n_dm + d;
   const unsigned long long* k = a.keys + bd * a.seg_per_bd + a.win_off[wi];
   double s = 0.0;
-  for (int i = threadIdx.x; i < nseg; i += NT) s += seg_rho(k[i], W, n_eff);
+  for (int i = threadIdx.x; i < nseg; i += NT) s += seg_rho(k[i], inv_wn);
   const double mu = nseg > 0 ? block_sum<NT>(s, red) / (double)nseg : 0.0;
   double ss = 0.0;
   for (int i = threadIdx.x; i < nseg; i += NT) {
-    const double dv = seg_rho(k[i], W, n_eff) - mu;
+    const double dv = seg_rho(k[i], inv_wn) - mu;
     ss = fma(dv, dv, ss);
   }
   const double sd = nseg > 0 ? sqrt(block_sum<NT>(ss, red) / (double)nseg) : 0.0;
@@ -319,11 +324,11 @@ __global__ void __launch_bounds__(256) select_kernel(const __grid_constant__ Bat
     st[1] = sd;
   }
   uint32_t* bits = a.bits + bd * a.word_per_bd + a.word_off[wi];
-  const double thresh = a.thresh;
+  const double thresh = a.thresh, inv_sd = seg_inv_sd(sd);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int base = warp * 32; base < nseg; base += NT) {
     const int i = base + lane;
-    const bool sel = i < nseg && seg_z(seg_rho(k[i], W, n_eff), mu, sd) >= thresh;
+    const bool sel = i < nseg && seg_z(seg_rho(k[i], inv_wn), mu, inv_sd) >= thresh;
     const uint32_t w = __ballot_sync(0xffffffffu, sel);
     if (lane == 0) bits[base / 32] = w;
   }
@@ -415,8 +420,8 @@ __global__ void __launch_bounds__(128) match_kernel(const __grid_constant__ Batc
     const int W = 1 << wlog[bw];
     const int end = bstart + W;
     const unsigned long long key = keys[woff[bw] + bsg];
-    const double rho = seg_rho(key, W, n_eff);
-    const double z = seg_z(rho, stats[bw * 2], stats[bw * 2 + 1]);
+    const double rho = seg_rho(key, seg_inv_wn(W, n_eff));
+    const double z = seg_z(rho, stats[bw * 2], seg_inv_sd(stats[bw * 2 + 1]));
     if (mask != 0 && bstart < g1) {
       g1 = max(g1, end);
       mask |= 1 << bw;
