@@ -409,11 +409,20 @@ def fill_segment(seg: volks_segment, wl, vis, cal=None, autos=None, bl_st=None,
         raise ValueError(f"vis shape {tuple(vis.shape)} does not hold [n_bl={seg.n_bl}][n_ap={seg.n_ap}]"
                          f"[n_f={wl.n_if * wl.n_chan}]")
     calc = None if cal is None else np.ascontiguousarray(cal, dtype=np.float64)
+    if calc is not None and calc.size != seg.n_pol * seg.n_bl * wl.n_if * 2:
+        raise ValueError(f"cal shape {calc.shape} does not hold [n_pol={seg.n_pol}][n_bl={seg.n_bl}]"
+                         f"[n_if={wl.n_if}][2]")
     seg.cal = None if calc is None else calc.ctypes.data_as(C.POINTER(C.c_double))
     keep = [keep_vis, calc]
     if autos is not None:
+        if len(autos.shape) != 4 or autos.shape[0] != seg.n_pol or \
+                tuple(autos.shape[2:]) != (seg.n_ap, wl.n_if * wl.n_chan):
+            raise ValueError(f"autos shape {tuple(autos.shape)} does not hold [n_pol={seg.n_pol}][n_st]"
+                             f"[n_ap={seg.n_ap}][n_f={wl.n_if * wl.n_chan}]")
         aptr, keep_a = _autos_pointer(autos)
         st = np.ascontiguousarray(bl_st, dtype=np.int32)
+        if st.shape != (seg.n_bl, 2):
+            raise ValueError(f"bl_st shape {st.shape} is not [n_bl={seg.n_bl}][2]")
         seg.autos = aptr
         seg.n_st = int(autos.shape[-3])
         seg.bl_st = st.ctypes.data_as(C.POINTER(C.c_int32))

@@ -207,3 +207,21 @@ def test_default_params_include_the_stride():
     wl = synth.small()
     import dataclasses
     assert V.make_params(dataclasses.replace(wl, stride=1)).stride == 1
+
+
+def test_binding_checks_cal_autos_and_station_pairs_against_the_descriptor():
+    wl = synth.small(n_bl=3, n_ap=20, n_if=4, n_chan=16)
+    seg = V.volks_segment()
+    vis2 = np.zeros((2, 3, 20, wl.n_f), dtype=np.complex64)
+    with pytest.raises(ValueError):   # one product's table for two products
+        V.fill_segment(seg, wl, vis2, np.zeros((3, wl.n_if, 2)))
+    V.fill_segment(seg, wl, vis2, np.zeros((2, 3, wl.n_if, 2)))
+    autos = np.ones((2, 3, 20, wl.n_f), dtype=np.float32)
+    st = np.array([[0, 1], [0, 2], [1, 2]])
+    keep = V.fill_segment(seg, wl, vis2, None, autos, st)
+    assert seg.n_st == 3
+    del keep
+    with pytest.raises(ValueError):
+        V.fill_segment(seg, wl, vis2, None, autos[:1], st)
+    with pytest.raises(ValueError):
+        V.fill_segment(seg, wl, vis2, None, autos, st[:2])
