@@ -146,3 +146,24 @@ def test_empty_and_invalid_arguments():
         V.volks_localize(*cols)
     cols[4][2] = 1.0                      # a NaN on an unused baseline is ignored
     assert V.volks_localize(*cols)["status"] == 0
+
+
+def test_matches_oracle_on_random_inputs():
+    """300 random cases: baseline counts 0-15, random partials (some
+    collinear), SNRs and lengths around the cuts, noise levels and one
+    injected bad delay in a third of them; every output field against the
+    oracle."""
+    rng = np.random.default_rng(2024)
+    for case in range(300):
+        n = int(rng.integers(0, 16))
+        pa = rng.normal(0, 5e-3, n)
+        pd = rng.normal(0, 5e-3, n) if case % 7 else 0.5 * pa
+        x = rng.normal(0, 3e-6, 2)
+        tau_cal = rng.normal(0, 1e-8, n)
+        tau = tau_cal + pa * x[0] + pd * x[1] + rng.normal(0, 10 ** rng.uniform(-12, -9), n)
+        if n and case % 3 == 0:
+            tau[int(rng.integers(0, n))] += 3e-8
+        snr = rng.uniform(3, 12, n)
+        length = rng.uniform(1e5, 3.5e6, n)
+        kw = dict(min_baselines=int(rng.integers(2, 5)), outlier_factor=float(rng.uniform(3, 8)))
+        check_vs_oracle([tau, tau_cal, pa, pd, snr, length], **kw)
