@@ -104,3 +104,34 @@ def test_two_rank_gloo_baseline_shards_match_single_process(tmp_path):
     assert sorted(map(_key, got["final"])) == sorted(map(_key, ref.candidates))
     assert got["tot"] == sum(len(p.P) for p in ref.peaks.values())
     assert got["tmax"] == 2.0
+
+
+def test_library_cross_match_equals_oracle_on_random_lists():
+    """400 random per-baseline candidate lists (1-6 DMs, 1-12 baselines,
+    intervals that chain, nest, touch or stand apart): the C cross-baseline
+    match keeps the same entries with the same baseline counts, in
+    (dm, t0, bl) order."""
+    from oracle import volks_oracle as O
+    rng = np.random.default_rng(99)
+    for case in range(400):
+        n_dm, n_bl = int(rng.integers(1, 7)), int(rng.integers(1, 13))
+        cands = []
+        for _ in range(int(rng.integers(0, 40))):
+            w = int(2 ** rng.integers(0, 6))
+            t0 = int(rng.integers(0, 200))
+            cands.append(dict(bl=int(rng.integers(0, n_bl)), dm_idx=int(rng.integers(0, n_dm)), win=w,
+                              seg=t0 // w, t0=t0, t1=t0 + w, g0=t0, g1=t0 + w, delay_idx=0, rate_idx=0,
+                              n_windows=2, peak_power=1.0, rho=1.0, z=float(rng.uniform(3, 9)),
+                              delay_s=0.0, rate_hz=0.0))
+        min_bl = int(rng.integers(1, 5))
+        by_dm = {}
+        for c in cands:
+            by_dm.setdefault(c["dm_idx"], []).append(c)
+        want = []
+        for d in sorted(by_dm):
+            want.extend(O.cross_baseline(by_dm[d], min_bl))
+        want = sorted(want, key=lambda c: (c["dm_idx"], c["t0"], c["bl"]))
+        got = V.volks_cross_match([_as_abi(c, np.arange(n_dm, dtype=float)) for c in cands], min_bl)
+        assert sorted(map(_key, got)) == sorted(map(_key, want)), case
+        assert [(c["dm_idx"], c["t0_ap"], c["bl"]) for c in got] == \
+            [(c["dm_idx"], c["t0"], c["bl"]) for c in want], case
