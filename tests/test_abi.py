@@ -77,6 +77,28 @@ def test_shift_table_bit_exact_vs_oracle(L, wl):
     assert np.array_equal(nv, [O.n_valid(wl.n_ap, r) for r in ref])
 
 
+def test_shift_table_bit_exact_vs_oracle_on_random_grids(L):
+    """200 random bands (64-2048 and 96-1536 points, 0.0625-2 MHz channels,
+    300 MHz-20 GHz), AP lengths and DM grids: identical integer shifts and
+    valid counts (both sides round the same FP64 expression half-up)."""
+    import dataclasses
+    rng = np.random.default_rng(5)
+    sizes = [64, 128, 256, 512, 1024, 2048, 96, 192, 384, 768, 1536]
+    for _ in range(200):
+        n_f = int(rng.choice(sizes))
+        bw = float(2.0 ** rng.integers(-4, 2))
+        wl = dataclasses.replace(synth.small(), n_if=1, n_chan=n_f, chan_bw_mhz=bw,
+                                 f_lo_mhz=float(rng.uniform(300, 20000)),
+                                 t_ap_s=float(rng.choice([1.024e-3, 0.512e-3, 2e-3, 1e-2])),
+                                 n_ap=int(rng.integers(1, 100000)), dm_lo=float(rng.uniform(0, 500)),
+                                 dm_step=float(rng.uniform(0.01, 20)), n_dm=int(rng.integers(1, 40)))
+        sh, nv = V.volks_shift_table(wl.f_lo_mhz, wl.chan_bw_mhz, n_f, wl.t_ap_s, wl.n_ap,
+                                     wl.dm_lo, wl.dm_step, wl.n_dm)
+        ref = O.shift_table(wl.f_lo_mhz, wl.chan_bw_mhz, n_f, wl.dms(), wl.t_ap_s)
+        assert np.array_equal(sh, ref)
+        assert np.array_equal(nv, [O.n_valid(wl.n_ap, r) for r in ref])
+
+
 def test_shift_table_large_dm_leaves_no_valid_ap(L):
     wl = synth.small(n_ap=40)
     sh, nv = V.volks_shift_table(wl.f_lo_mhz, wl.chan_bw_mhz, wl.n_f, wl.t_ap_s, 40,
