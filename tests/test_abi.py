@@ -41,6 +41,9 @@ def test_exports_every_declared_symbol(L):
     assert not missing, missing
     for n in names:
         assert hasattr(L, n)
+    # and nothing with the ABI's prefix is exported without a declaration
+    undeclared = sorted(exported - set(names))
+    assert not undeclared, undeclared
 
 
 def test_struct_layout_matches_c(L):
