@@ -53,3 +53,17 @@ def test_calibration_on_grid_draws_grid_delays():
     cal = synth.draw_calibration_on_grid(wl, np.random.default_rng(11))
     cells = cal[..., 0] * (4 * wl.n_chan * wl.chan_bw_mhz * 1e6)
     np.testing.assert_allclose(cells, np.round(cells), atol=1e-9)
+
+
+def test_bench_flop_and_trial_counts_by_hand():
+    """The nominal counts behind the reported roofline: 1 baseline, 64
+    points (M = 256), windows 1 and 2, 10 dedispersed APs.
+      delay FFTs   10 x 5 x 256 x log2 256          = 102,400
+      w = 1        10 segments x 256 cells x 3       =   7,680
+      w = 2        5 x 256 columns x 5 x 8 x log2 8  = 153,600
+                   + 5 x 8 x 256 cells x 3           =  30,720
+    total 294,400 flops; trials 10 + 5 = 15."""
+    import bench
+    wl = synth.small(n_bl=1, n_ap=10, n_if=4, n_chan=16, n_dm=1, windows=(1, 2))
+    assert bench.algorithmic_flops(wl, [10]) == 294400.0
+    assert bench.trial_count(wl, [10]) == 15
