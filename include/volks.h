@@ -570,12 +570,15 @@ int volks_localize(const volks_loc_obs *obs, int32_t n, const volks_loc_params *
  * device array of VOLKS_NOALLOC_SCRATCH_BYTES that every device which loads
  * this library holds until the process exits.
  *
- *   seg->vis      device memory (host pointers are rejected), as for
+ *   seg->vis      device memory of the current device (host pointers and
+ *                 other devices' memory are rejected), as for
  *                 volks_search_segment; seg->cal host memory or NULL, at
  *                 most 256 (n_bl * n_if) entries.
- *   peak_power    device, float [n_bl][n_dm][S]: max |Z|^2 of the segment.
- *   peak_cell     device, int32 [n_bl][n_dm][S]: q * M + m of that cell
- *                 (unsigned rate cell q, delay cell m, M = pad_delay*n_f).
+ *   peak_power    device memory of the current device, float
+ *                 [n_bl][n_dm][S]: max |Z|^2 of the segment.
+ *   peak_cell     device memory of the current device, int32
+ *                 [n_bl][n_dm][S]: q * M + m of that cell (unsigned rate
+ *                 cell q, delay cell m, M = pad_delay*n_f).
  *   S = sum_i floor(n_ap / win[i]); window i's segments start at
  *   sum_{j<i} floor(n_ap / win[j]); segment s of window i exists while
  *   s < max(0, n_valid) / win[i] (n_valid as in volks_shift_table); the
@@ -600,6 +603,20 @@ int volks_localize(const volks_loc_obs *obs, int32_t n, const volks_loc_params *
 
 int volks_search_peaks_noalloc(const volks_segment *seg, const volks_params *prm,
                                void *cuda_stream, float *peak_power, int32_t *peak_cell);
+
+/*
+ * Checking accessor of the no-allocation variant (no paper counterpart):
+ * copies the shift table (int32 [n_dm][n_f]) and n_valid (int32 [n_dm])
+ * that the last volks_search_peaks_noalloc call on the current device
+ * computed on the GPU into caller device buffers, on cuda_stream (device
+ * to device copies; nothing is allocated).  n_dm and n_f must be the last
+ * call's; VOLKS_EINVAL if they are not, if no call has run on the device,
+ * or if a buffer is not device memory of the current device.  The copies
+ * read the shared scratch, so they race with a later call that overlaps
+ * them on the GPU.
+ */
+int volks_noalloc_tables(void *cuda_stream, int32_t *shifts, int32_t *nvalid, int32_t n_dm,
+                         int32_t n_f);
 
 /*
  * Measured FP32 FMA throughput of the current device in TFLOP/s (2 flops

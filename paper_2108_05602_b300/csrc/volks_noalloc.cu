@@ -45,6 +45,15 @@ constexpr double kTwoPiNA = 6.283185307179586476925286766559;
 std::mutex g_mu;
 void* g_dev_ptr[kMaxDevices] = {};
 
+// Where the last call on each device left its shift table in the scratch
+// (read back by volks_noalloc_tables).
+struct LastTables {
+  size_t o_shifts, o_nvalid;
+  int n_dm, n_f;
+  bool set;
+};
+LastTables g_last[kMaxDevices] = {};
+
 // Errors go to the library's thread-local message (volks_last_error()).
 int na_fail(int code, const char* fmt, ...) {
   char buf[512];
@@ -77,6 +86,22 @@ int scratch_ptr(void** out) {
 
 bool pow2(long long x) { return x > 0 && (x & (x - 1)) == 0; }
 
+// A caller buffer must be device (or managed) memory of the current device:
+// a host pointer would fault in the kernels that write it, and another
+// device's memory would be reached through peer access that may not be on.
+int device_buffer(const void* p, int dev, const char* name) {
+  cudaPointerAttributes attr{};
+  if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+    cudaGetLastError();
+    return na_fail(VOLKS_EINVAL, "%s: not a CUDA allocation", name);
+  }
+  if (!(attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged))
+    return na_fail(VOLKS_EINVAL, "%s must be device memory for the no-allocation entry point", name);
+  if (attr.device != dev)
+    return na_fail(VOLKS_EINVAL, "%s is on device %d; the current device is %d", name, attr.device, dev);
+  return 0;
+}
+
 struct TableArgs {
   double f_lo_mhz, chan_bw_mhz, t_ap_s, dm_lo, dm_step;
   int n_bl, n_if, n_chan, n_f, n_dm, n_ap, M, has_cal;
@@ -87,6 +112,10 @@ struct TableArgs {
   float2* tw_m;
   double cal[kMaxCal][2];
 };
+// TableArgs is passed by value as a kernel parameter (about 4.2 KB): above
+// the classic 4 KB limit, within the 32,764-byte limit that CUDA 12.1+
+// toolkits allow on Volta and later GPUs.
+static_assert(sizeof(TableArgs) <= 32764, "kernel parameter block too large");
 
 // Shift table with the same FP64 operation order as the host's table
 // (round-to-nearest intrinsics, no contraction), one block per DM trial.
@@ -248,16 +277,23 @@ extern "C" int volks_search_peaks_noalloc(const volks_segment* seg, const volks_
                    "segment needs %zu bytes of scratch; the no-allocation entry point has %zu "
                    "(use volks_search_segment)", off, (size_t)VOLKS_NOALLOC_SCRATCH_BYTES);
   if (!seg->vis) return na_fail(VOLKS_EINVAL, "vis is NULL");
-  cudaPointerAttributes attr{};
-  if (cudaPointerGetAttributes(&attr, seg->vis) != cudaSuccess ||
-      !(attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged)) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
-    return na_fail(VOLKS_EINVAL, "vis must be device memory for the no-allocation entry point");
+    return na_fail(VOLKS_EINVAL, "no current CUDA device");
   }
+  int rc = device_buffer(seg->vis, dev, "vis");
+  if (!rc) rc = device_buffer(peak_power, dev, "peak_power");
+  if (!rc) rc = device_buffer(peak_cell, dev, "peak_cell");
+  if (rc) return rc;
 
   void* base = nullptr;
-  int rc = scratch_ptr(&base);
+  rc = scratch_ptr(&base);
   if (rc) return rc;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_last[dev] = LastTables{o_shifts, o_nvalid, n_dm, (int)n_f, true};
+  }
   unsigned char* sp = static_cast<unsigned char*>(base);
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   int n_launch = 0;
@@ -351,4 +387,35 @@ extern "C" int volks_search_peaks_noalloc(const volks_segment* seg, const volks_
   }
   na_unpack_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(ua);
   return cu(cudaGetLastError(), "unpack kernel");
+}
+
+extern "C" int volks_noalloc_tables(void* cuda_stream, int32_t* shifts, int32_t* nvalid, int32_t n_dm,
+                                    int32_t n_f) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return na_fail(VOLKS_EINVAL, "no current CUDA device");
+  }
+  if (dev < 0 || dev >= kMaxDevices) return na_fail(VOLKS_EINVAL, "device ordinal %d out of range", dev);
+  LastTables lt;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    lt = g_last[dev];
+  }
+  if (!lt.set) return na_fail(VOLKS_EINVAL, "no no-allocation search has run on device %d", dev);
+  if (n_dm != lt.n_dm || n_f != lt.n_f)
+    return na_fail(VOLKS_EINVAL, "last call had n_dm %d, n_f %d (asked %d, %d)", lt.n_dm, lt.n_f, n_dm, n_f);
+  if (lt.n_dm == 0) return 0;
+  int rc = device_buffer(shifts, dev, "shifts");
+  if (!rc) rc = device_buffer(nvalid, dev, "nvalid");
+  if (rc) return rc;
+  void* base = nullptr;
+  if ((rc = scratch_ptr(&base))) return rc;
+  const unsigned char* sp = static_cast<const unsigned char*>(base);
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e = cudaMemcpyAsync(shifts, sp + lt.o_shifts, (size_t)lt.n_dm * lt.n_f * sizeof(int32_t),
+                                  cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(nvalid, sp + lt.o_nvalid, (size_t)lt.n_dm * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
+  return e == cudaSuccess ? 0 : na_fail(VOLKS_ECUDA, "copy tables: %s", cudaGetErrorString(e));
 }

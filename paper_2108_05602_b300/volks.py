@@ -169,6 +169,8 @@ def lib() -> C.CDLL:
     L.volks_search_peaks_noalloc.argtypes = [C.POINTER(volks_segment), C.POINTER(volks_params),
                                              P, P, P]
     L.volks_search_peaks_noalloc.restype = C.c_int
+    L.volks_noalloc_tables.argtypes = [P, P, P, I32, I32]
+    L.volks_noalloc_tables.restype = C.c_int
     L.volks_fringe_fit_calibrator.argtypes = [C.POINTER(volks_segment), I32, P, C.POINTER(C.c_double),
                                               C.POINTER(C.c_double)]
     L.volks_fringe_fit_calibrator.restype = C.c_int
@@ -240,6 +242,13 @@ def volks_search_peaks_noalloc(seg: volks_segment, prm: volks_params, stream: in
                                             C.c_void_p(peak_power_ptr),
                                             C.c_void_p(peak_cell_ptr)),
            "volks_search_peaks_noalloc")
+
+
+def volks_noalloc_tables(stream: int, shifts_ptr: int, nvalid_ptr: int, n_dm: int, n_f: int):
+    """Copy the last no-allocation call's device shift table and n_valid
+    into caller device buffers (a checking accessor)."""
+    _check(lib().volks_noalloc_tables(C.c_void_p(stream), C.c_void_p(shifts_ptr),
+                                      C.c_void_p(nvalid_ptr), n_dm, n_f), "volks_noalloc_tables")
 
 
 def volks_fringe_fit_calibrator(wl, vis, pad: int = 4, stream: int = 0, n_bl=None, n_ap=None):

@@ -250,3 +250,26 @@ def test_binding_checks_cal_autos_and_station_pairs_against_the_descriptor():
         V.fill_segment(seg, wl, vis2, None, autos[:1], st)
     with pytest.raises(ValueError):
         V.fill_segment(seg, wl, vis2, None, autos, st[:2])
+
+
+def test_noalloc_rejects_host_buffers_before_any_launch(L):
+    """The no-allocation entry point refuses host memory for its input and
+    outputs with VOLKS_EINVAL before it launches anything (on a machine
+    without a GPU every pointer fails the check; the GPU test file checks
+    the messages on a device)."""
+    wl = synth.small(n_bl=1, n_ap=64, n_if=4, n_chan=16, n_dm=2, windows=(1, 2))
+    prm = V.make_params(wl)
+    spb = sum(wl.n_ap // w for w in wl.windows)
+    vis = np.zeros((1, wl.n_ap, wl.n_f), dtype=np.complex64)
+    pw = np.zeros((wl.n_bl, wl.n_dm, spb), dtype=np.float32)
+    cl = np.zeros((wl.n_bl, wl.n_dm, spb), dtype=np.int32)
+    seg = V.volks_segment(wl.n_bl, wl.n_ap, wl.n_if, wl.n_chan, wl.t_ap_s, wl.f_lo_mhz,
+                          wl.chan_bw_mhz, vis.ctypes.data, None)
+    rc = L.volks_search_peaks_noalloc(C.byref(seg), C.byref(prm), None, C.c_void_p(pw.ctypes.data),
+                                      C.c_void_p(cl.ctypes.data))
+    assert rc == V.VOLKS_EINVAL and L.volks_last_error()
+    sh = np.zeros((wl.n_dm, wl.n_f), dtype=np.int32)
+    nv = np.zeros(wl.n_dm, dtype=np.int32)
+    rc = L.volks_noalloc_tables(None, C.c_void_p(sh.ctypes.data), C.c_void_p(nv.ctypes.data),
+                                wl.n_dm, wl.n_f)
+    assert rc == V.VOLKS_EINVAL

@@ -14,6 +14,7 @@ Tolerances (FP32 path):
     Z_TOL = 1e-4 of the threshold or of another member's z.
 """
 import math
+import zlib
 
 import numpy as np
 import pytest
@@ -164,7 +165,7 @@ def test_peaks_stats_candidates_match_oracle(cfg):
     cfg = dict(cfg)
     name = cfg.pop("name")
     wl = synth.small(**cfg, name=name, min_baselines=1)
-    vis, cal, _ = make_data(wl, seed=hash(name) % 1000)
+    vis, cal, _ = make_data(wl, seed=zlib.crc32(name.encode()) % 1000)
     g = gpu_search(wl, vis, cal)
     ref = O.search(wl, vis, cal)
     sh, nv = g.shifts()
@@ -333,7 +334,12 @@ def test_evn_full_size_sampled_parity():
     t = g.timing()
     assert t.n_search_launches >= 1
     rng = np.random.default_rng(0)
-    shifts, nvalid = g.shifts()
+    # the oracle's own shift table drives its dedispersion; the library's
+    # table must equal it bit for bit
+    shifts = O.shift_table(wl.f_lo_mhz, wl.chan_bw_mhz, wl.n_f, wl.dms(), wl.t_ap_s)
+    nvalid = np.array([O.n_valid(wl.n_ap, row) for row in shifts])
+    g_shifts, g_nvalid = g.shifts()
+    assert np.array_equal(g_shifts, shifts) and np.array_equal(g_nvalid, nvalid)
     samples = []
     for p in pulses[:4]:
         d = int(np.argmin(np.abs(wl.dms() - p.dm)))
