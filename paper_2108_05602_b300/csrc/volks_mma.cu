@@ -52,6 +52,8 @@ constexpr int kTmemCols = 512;       // two job buffers
 constexpr uint32_t kGemmMask = 0x3cu;  // windows on the tensor cores: 4, 8, 16, 32 (log2 2..5)
 constexpr int kGemmSegs = 15;        // their segments in a tile
 constexpr int kTopK = 8;             // most delay cells refined per segment and unit
+constexpr int kPerBlk = 6;           // most delay cells a 128-cell block adds to a segment's list
+constexpr int kList = 24;            // candidate list length per segment (>= 4 blocks x kPerBlk)
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
 template <int PREC>
@@ -70,6 +72,8 @@ struct Op {
     return o;
   }
   static constexpr int B_BYTES = b_off(6);
+  // the search keeps only windows 4..32 (log2 2..5) on the tensor cores
+  static constexpr int B_SEARCH = b_off(6) - b_off(2);
   // operand scale target for the per-tile power-of-two scaling
   static constexpr int SCALE_EXP = PREC == VOLKS_FP8 ? 8 : 14;
 };
@@ -80,12 +84,13 @@ struct MmaSmem {
   static constexpr size_t S_BYTES = (size_t)32 * (N + 1) * sizeof(float2);
   static constexpr size_t OFF_A = (S_BYTES + 1023) & ~(size_t)1023;
   static constexpr size_t OFF_B = OFF_A + 2 * Op<PREC>::A_BYTES;
-  static constexpr size_t OFF_COL = OFF_B + Op<PREC>::B_BYTES;                 // u32 [15][128]
-  static constexpr size_t OFF_CAND = OFF_COL + (size_t)kGemmSegs * kMRows * 4;  // uint2 [31][8]
-  static constexpr size_t OFF_CCOUNT = OFF_CAND + (size_t)kGemmSegs * kTopK * 8;  // int [31]
-  static constexpr size_t OFF_RUNMAX = OFF_CCOUNT + 128;                         // u32 [31]
-  static constexpr size_t OFF_BEST = OFF_RUNMAX + 128;                           // u64 [63]
-  static constexpr size_t USED = OFF_BEST + (size_t)kMaxSegPerTile * 8;
+  static constexpr size_t OFF_COL = OFF_B + Op<PREC>::B_SEARCH;                    // u32 [2][15][128]
+  static constexpr size_t OFF_LIST = OFF_COL + (size_t)2 * kGemmSegs * kMRows * 4;  // uint2 [15][kList]
+  static constexpr size_t OFF_LCOUNT = OFF_LIST + (size_t)kGemmSegs * kList * 8;    // int [15]
+  static constexpr size_t OFF_RUNMAX = OFF_LCOUNT + 64;                             // u32 [15]
+  static constexpr size_t OFF_BEST = OFF_RUNMAX + 64;                               // u64 [63]
+  static constexpr size_t OFF_PIECE = OFF_BEST + (size_t)kMaxSegPerTile * 8;        // int
+  static constexpr size_t USED = OFF_PIECE + 8;
   // more than half an SM's shared memory: one CTA per SM, so the 512-column
   // TMEM allocation never waits on another CTA
   static constexpr size_t BYTES = USED > 120 * 1024 ? USED : 120 * 1024;
@@ -112,16 +117,16 @@ __device__ __forceinline__ uint32_t e4m3x2(float a, float b) {
 // (Re, Im) of AP u, so that D = A B^T gives (Re, Im) of
 // Z_q = sum_u Y_u exp(-2 pi i q u / R), R = 4w.  Segments sharing one MMA
 // (K of a segment shorter than one MMA) get a block-diagonal B.
-template <int PREC>
+template <int PREC, int L0 = 1>
 __device__ void build_rate_dft(uint8_t* B, const float2* __restrict__ tw_m, int M, int tid, int nt) {
   using O = Op<PREC>;
   constexpr int EB = O::EB;
 #pragma unroll 1
-  for (int l = 1; l <= 5; ++l) {
+  for (int l = L0; l <= 5; ++l) {
     const int w = 1 << l, R = 4 * w;
     const int rows = O::b_rows(l), kel = O::b_row_bytes(l) / EB;
     const uint32_t rb = (uint32_t)O::b_row_bytes(l);
-    uint8_t* base = B + O::b_off(l);
+    uint8_t* base = B + O::b_off(l) - O::b_off(L0);
 #pragma unroll 1
     for (int i = tid; i < rows * kel; i += nt) {
       const int n = i / kel, k = i % kel;
@@ -306,197 +311,231 @@ __device__ __forceinline__ unsigned long long warp_key(float p, uint32_t lin) {
   return seg_key(wmax, wlin);
 }
 
+// Per-thread pipeline state that persists across work units: the TMEM base,
+// the jobs issued into each buffer (issuing thread) and one phase-parity bit
+// per barrier this thread waits on (bit PB_*: + buffer index).
 struct MmaCtx {
   uint32_t tmem;        // TMEM base address (512 columns)
-  uint32_t f_par[2];    // consumers: parity of the next completion of each job buffer
-  uint32_t n_use[2];    // producer: jobs issued into each buffer so far
-  uint32_t a_par[2];    // producer: parity of the next pack of each A buffer
+  uint32_t par;         // parity bits, see PB_*
+  uint32_t n_use0, n_use1;
 };
+constexpr int PB_FULL = 0, PB_AFULL = 2, PB_CFREE = 4, PB_ADONE = 6, PB_CDONE = 8;
+__device__ __forceinline__ uint32_t pbit(uint32_t par, int b) { return (par >> b) & 1u; }
 
 struct JobTable {
   MmaOp ops[6][kMaxOpsPerJob];  // by window log2 (1..5)
   int n_ops[6];
+  uint64_t bd[6];               // B descriptor of each window
+  uint64_t ad[2];               // A descriptor of each A buffer
 };
 
 struct MmaBars {
-  uint64_t full[2];     // MMAs of the job in TMEM buffer i completed (tcgen05.commit)
-  uint64_t empty[2];    // every consumer warp has drained TMEM buffer i
-  uint64_t afull[2];    // every consumer warp has packed its share of A buffer i
+  uint64_t full[2];     // the MMAs of the job in TMEM buffer i completed (tcgen05.commit)
+  uint64_t empty[2];    // the drain warpgroup of buffer i has read it
+  uint64_t afull[2];    // the helper warps packed A buffer i
+  uint64_t adone[2];    // every MMA reading A buffer i completed (commit after a block's last job)
+  uint64_t cdone[2];    // every drain warp wrote its rows of column-maxima buffer i
+  uint64_t cfree[2];    // the helper warps merged column-maxima buffer i (it may be rewritten)
 };
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
 }
-// Barrier 1 over the consumer warps only (the producer warp keeps issuing).
-template <int NTHREADS>
-__device__ __forceinline__ void consumer_sync() {
-  asm volatile("bar.sync 1, %0;" ::"n"(NTHREADS) : "memory");
+
+// One warp-wide bounded wait (lane 0 polls, the result is broadcast).
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, int lane) {
+  bool w = true;
+  if (lane == 0) w = tc::mbar_wait_bounded(bar, parity, kWaitCycles);
+  return __shfl_sync(0xffffffffu, w, 0) != 0;
 }
 
-// Candidate delay cells of a segment (per CTA unit): the cells whose coarse
-// power is at least kKeep[PREC] times the segment's coarse maximum, at most
-// kTopK of them (the largest; ties to the lower cell).  kKeep = 1 - delta,
-// delta ~4x the coarse relative error of |Z|^2 at a peak for the operand
-// type, so the FP32 peak's cell is retained unless more than kTopK cells
-// lie within delta of the coarse maximum.
+// Warp-wide wait that does other work meanwhile: while the phase is not
+// complete, run work pieces (`piece()` returns false when none is left),
+// then fall back to the bounded wait.
+template <class F>
+__device__ __forceinline__ bool warp_wait_busy(uint64_t* bar, uint32_t parity, int lane, F&& piece) {
+  for (;;) {
+    bool done = false;
+    if (lane == 0) done = tc::mbar_test(bar, parity);
+    if (__shfl_sync(0xffffffffu, done, 0)) return true;
+    if (!piece()) return warp_wait(bar, parity, lane);
+  }
+}
+
+// max |Z|^2 over the 16 cells of a 32-column chunk ((Re, Im) column pairs)
+__device__ __forceinline__ float fold32(const uint32_t (&v)[32]) {
+  float ma = 0.f, mb = 0.f;
+#pragma unroll
+  for (int i = 0; i < 32; i += 8) {
+    const float a0 = __uint_as_float(v[i]), a1 = __uint_as_float(v[i + 1]);
+    const float a2 = __uint_as_float(v[i + 2]), a3 = __uint_as_float(v[i + 3]);
+    const float b0 = __uint_as_float(v[i + 4]), b1 = __uint_as_float(v[i + 5]);
+    const float b2 = __uint_as_float(v[i + 6]), b3 = __uint_as_float(v[i + 7]);
+    ma = tc::fmax3(ma, fmaf(a0, a0, a1 * a1), fmaf(a2, a2, a3 * a3));
+    mb = tc::fmax3(mb, fmaf(b0, b0, b1 * b1), fmaf(b2, b2, b3 * b3));
+  }
+  return fmaxf(ma, mb);
+}
+
+// Drain one job (window 2^L, 256 TMEM columns) for this warp's 32 rows: the
+// eight 32-column chunks are loaded two at a time (the next load in flight
+// while the previous chunk is folded), the buffer is handed back to the
+// issuing thread after the last load, and the largest coarse |Z|^2 of each
+// segment (8 w columns) is stored for this row at cm[s * kMRows].
+template <int L>
+__device__ __forceinline__ void drain_job(uint32_t tb, uint32_t* cm, uint64_t* empty, int lane) {
+  constexpr int SEGC = 8 << L;  // columns per segment
+  constexpr int CPS = SEGC / 32;  // chunks per segment
+  static_assert(SEGC >= 32, "a chunk lies within one segment");
+  uint32_t va[32], vb[32];
+  float m = 0.f;
+  tc::tmem_ld32(tb, va);
+  tc::tmem_wait_ld_dep(va);
+#pragma unroll
+  for (int ch = 0; ch < 8; ch += 2) {
+    tc::tmem_ld32(tb + (uint32_t)(ch + 1) * 32u, vb);
+    m = fmaxf(m, fold32(va));
+    if ((ch + 1) % CPS == 0) {
+      cm[(ch / CPS) * kMRows] = __float_as_uint(m);
+      m = 0.f;
+    }
+    tc::tmem_wait_ld_dep(vb);
+    if (ch + 2 < 8) {
+      tc::tmem_ld32(tb + (uint32_t)(ch + 2) * 32u, va);
+    } else {
+      // every load of the job is complete: hand the buffer back
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(empty);
+    }
+    m = fmaxf(m, fold32(vb));
+    if ((ch + 2) % CPS == 0) {
+      cm[((ch + 1) / CPS) * kMRows] = __float_as_uint(m);
+      m = 0.f;
+    }
+    if (ch + 2 < 8) tc::tmem_wait_ld_dep(va);
+  }
+}
+
+// Candidate delay cells of a segment (per work unit): the cells whose coarse
+// power is at least Keep<PREC> times the segment's coarse maximum, at most
+// kTopK of them.  Keep = 1 - delta, delta ~4x the coarse relative error of
+// |Z|^2 at a peak for the operand type, so the FP32 peak's cell is retained
+// unless more than kTopK cells lie within delta of the coarse maximum (then
+// delta is halved, a few times at most, and the lowest cells are kept).
 template <int PREC>
 struct Keep {
   static constexpr float value = PREC == VOLKS_FP8 ? 1.0f - 1.0f / 4 : PREC == VOLKS_FP16 ? 1.0f - 1.0f / 64 : 1.0f - 1.0f / 16;
 };
 
-// Merge the coarse column maxima of one 128-cell block (v[i] at cell
-// c[i], four per lane) into segment sg's candidate list (one warp).
+// Append the cells of one 128-cell block (column maxima cm[cell]) that lie
+// within delta of the segment's running maximum (this block included) to the
+// segment's list, at most kPerBlk of them (delta halved while more pass, then
+// the lowest cells).  The running maximum only grows, so the list holds
+// every cell that the final threshold (`finish_list`) can keep.  One warp.
 template <int PREC>
-__device__ __forceinline__ void merge_block(uint32_t (&v)[4], uint32_t (&c)[4], uint2* cand, int* ccount,
+__device__ __forceinline__ void merge_block(const uint32_t* __restrict__ cm, int b, uint2* lst, int* lcount,
                                             uint32_t* runmax, int sg, int lane) {
-  const int on = ccount[sg];
-  uint32_t ov = 0u, oc = 0xffffffffu;
-  if (lane < on) {
-    const uint2 t = cand[sg * kTopK + lane];
-    ov = t.x;
-    oc = t.y;
-  }
-  uint32_t bm = max(max(v[0], v[1]), max(v[2], v[3]));
-  bm = __reduce_max_sync(0xffffffffu, bm);
+  uint32_t v[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = cm[lane + 32 * i];
+  const uint32_t bm = __reduce_max_sync(0xffffffffu, max(max(v[0], v[1]), max(v[2], v[3])));
   const uint32_t mx = max(runmax[sg], bm);
-  // margin: 1 - Keep, halved while more than kTopK cells pass (at most a few
-  // times; exact ties beyond kTopK fall through to the top-kTopK selection)
   float keep = Keep<PREC>::value;
-  uint32_t thr;
-  bool ko, kn[4];
-  uint32_t bo, bn[4];
+  bool kn[4];
+  uint32_t bn[4];
   int total;
 #pragma unroll 1
   for (int it = 0;; ++it) {
-    thr = __float_as_uint(__uint_as_float(mx) * keep);
-    ko = lane < on && ov >= thr;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) kn[i] = v[i] >= thr;
-    bo = __ballot_sync(0xffffffffu, ko);
-    total = __popc(bo);
+    const uint32_t thr = __float_as_uint(__uint_as_float(mx) * keep);
+    total = 0;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
+      kn[i] = v[i] >= thr;
       bn[i] = __ballot_sync(0xffffffffu, kn[i]);
       total += __popc(bn[i]);
     }
-    if (total <= kTopK || it == 6) break;
+    if (total <= kPerBlk || it == 6) break;
     keep = 0.5f * (1.0f + keep);
   }
-  __syncwarp();
-  if (total <= kTopK) {
-    const uint32_t lt = (1u << lane) - 1u;
-    int base = 0;
-    if (ko) cand[sg * kTopK + base + __popc(bo & lt)] = make_uint2(ov, oc);
-    base += __popc(bo);
+  // cell = 128 b + lane + 32 i: ballot order (i, then lane) is cell order
+  const int base = lcount[sg];
+  const uint32_t lt = (1u << lane) - 1u;
+  int pos = base;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      if (kn[i]) cand[sg * kTopK + base + __popc(bn[i] & lt)] = make_uint2(v[i], c[i]);
-      base += __popc(bn[i]);
-    }
-  } else {
-    // the kTopK largest of the retained cells (value, then lower cell)
-    if (!ko) {
-      ov = 0u;
-      oc = 0xffffffffu;
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-      if (!kn[i]) {
-        v[i] = 0u;
-        c[i] = 0xffffffffu;
-      }
-    uint2 out = make_uint2(0u, 0xffffffffu);
-#pragma unroll 1
-    for (int rr = 0; rr < kTopK; ++rr) {
-      uint32_t bv = ov, bc = oc;
-      int bi = 4;
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-        if (v[i] > bv || (v[i] == bv && c[i] < bc)) {
-          bv = v[i];
-          bc = c[i];
-          bi = i;
-        }
-      const uint32_t wv = __reduce_max_sync(0xffffffffu, bv);
-      const uint32_t wc = __reduce_min_sync(0xffffffffu, bv == wv ? bc : 0xffffffffu);
-      if (lane == rr) out = make_uint2(wv, wc);
-      if (bv == wv && bc == wc) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-          if (bi == i) {
-            v[i] = 0u;
-            c[i] = 0xffffffffu;
-          }
-        if (bi == 4) {
-          ov = 0u;
-          oc = 0xffffffffu;
-        }
-      }
-    }
-    if (lane < kTopK) cand[sg * kTopK + lane] = out;
-    total = kTopK;
+  for (int i = 0; i < 4; ++i) {
+    const int p = pos + __popc(bn[i] & lt);
+    if (kn[i] && p < base + kPerBlk) lst[sg * kList + p] = make_uint2(v[i], (uint32_t)(b * kMRows + lane + 32 * i));
+    pos += __popc(bn[i]);
   }
   __syncwarp();
   if (lane == 0) {
-    ccount[sg] = total;
+    lcount[sg] = base + min(total, kPerBlk);
     runmax[sg] = mx;
   }
   __syncwarp();
 }
 
-// Drain this warp's 32-column chunks [ch0, ch1) of one job (window 2^L) from
-// TMEM: load, hand the buffer back to the producer (mbarrier `empty`),
-// then fold coarse |Z|^2 into the per-segment column maxima cm[s * 128]
-// (segment s of the window = columns 8 w s .. 8 w s + 8 w - 1).
-template <int L>
-__device__ __forceinline__ void drain_job(uint32_t tb, uint32_t* cm, int ch0, int ch1, uint64_t* empty,
-                                          int lane) {
-  constexpr int SEGC = 8 << L;  // columns per segment
-  static_assert(SEGC >= 32, "a chunk lies within one segment");
-  // max |Z|^2 over the 16 cells of a 32-column chunk, two independent chains
-  auto fold = [&](const uint32_t (&v)[32]) {
-    float ma = 0.f, mb = 0.f;
-#pragma unroll
-    for (int i = 0; i < 32; i += 8) {
-      const float a0 = __uint_as_float(v[i]), a1 = __uint_as_float(v[i + 1]);
-      const float a2 = __uint_as_float(v[i + 2]), a3 = __uint_as_float(v[i + 3]);
-      const float b0 = __uint_as_float(v[i + 4]), b1 = __uint_as_float(v[i + 5]);
-      const float b2 = __uint_as_float(v[i + 6]), b3 = __uint_as_float(v[i + 7]);
-      ma = tc::fmax3(ma, fmaf(a0, a0, a1 * a1), fmaf(a2, a2, a3 * a3));
-      mb = tc::fmax3(mb, fmaf(b0, b0, b1 * b1), fmaf(b2, b2, b3 * b3));
-    }
-    return fmaxf(ma, mb);
-  };
+// Final candidates of a segment from its list: the entries within delta of
+// the segment's coarse maximum (delta halved while more than kTopK pass,
+// then the lowest cells), compacted to the front of the list; returns their
+// number.  One warp.
+template <int PREC>
+__device__ __forceinline__ int finish_list(uint2* lst, const int* lcount, const uint32_t* runmax, int sg, int lane) {
+  const int n = lcount[sg];
+  const uint2 e = lane < n ? lst[sg * kList + lane] : make_uint2(0u, 0xffffffffu);
+  const uint32_t mx = runmax[sg];
+  float keep = Keep<PREC>::value;
+  bool k;
+  uint32_t bal;
+  int total;
 #pragma unroll 1
-  for (int ch = ch0; ch < ch1; ++ch) {
-    uint32_t v[32];
-    tc::tmem_ld32(tb + (uint32_t)ch * 32u, v);
-    tc::tmem_wait_ld();
-    if (ch + 1 == ch1) {
-      // accumulators are in registers: release the TMEM buffer
-      tc::fence_before_sync();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(empty);
-    }
-    atomicMax(cm + ((ch * 32) / SEGC) * kMRows, __float_as_uint(fold(v)));
+  for (int it = 0;; ++it) {
+    const uint32_t thr = __float_as_uint(__uint_as_float(mx) * keep);
+    k = lane < n && e.x >= thr;
+    bal = __ballot_sync(0xffffffffu, k);
+    total = __popc(bal);
+    if (total <= kTopK || it == 6) break;
+    keep = 0.5f * (1.0f + keep);
   }
+  const int p = __popc(bal & ((1u << lane) - 1u));
+  __syncwarp();
+  if (k && p < kTopK) lst[sg * kList + p] = e;
+  __syncwarp();
+  return min(total, kTopK);
 }
 
 // One unit on the tensor-core path.  Returns false if a bounded wait gave
 // up (the error flag is set; the caller stops).
+//
+// Warp roles during the GEMM phase (NW warps):
+//   warp 0, lane 0   issues every job's MMAs once its TMEM buffer is free and
+//                    its A block packed, then commits to the job's `full`
+//                    barrier (and, after a block's last job, to `adone`);
+//   drain warps      warps 4 .. 4 + 4 NWG - 1: one warpgroup per TMEM buffer
+//                    (two when NW = 16, so jobs alternate between them; one
+//                    that takes every job when NW = 8); each warp reads the
+//                    whole job for its 32 TMEM lanes (lane quarter = warp % 4)
+//                    and stores per-(segment, delay cell) coarse maxima into
+//                    one of two column-maxima buffers (by block parity);
+//   helper warps     the others: the exact 1- and 2-AP windows, the A blocks
+//                    from the third on (once `adone` says the MMAs reading the
+//                    buffer are complete), and the candidate merges of each
+//                    block (once every drain warp passed `cdone`).
 template <int N1, int FOLD, int PREC>
 __device__ __forceinline__ bool mma_tile(const UnitState& us, uint8_t* smem, MmaCtx& cx, MmaBars& bars,
                                          const JobTable& jt, float* s_amax, unsigned int* err) {
   using O = Op<PREC>;
   using L = MmaSmem<N1, PREC>;
   constexpr int N = 32 * N1, LD = N + 1, NT = N, NW = N1, NMB = N / kMRows;
-  constexpr int NC = NW - 1;            // consumer warps (warp 0 issues the MMAs)
+  constexpr int NWG = NW >= 16 ? 2 : 1;      // drain warpgroups
+  constexpr int NHELP = NW - 1 - 4 * NWG;    // helper warps
+  static_assert(NHELP >= 1 && NMB >= 2, "work split");
   float2* S = reinterpret_cast<float2*>(smem);
   uint8_t* A = smem + L::OFF_A;
-  uint8_t* Bm = smem + L::OFF_B;
   uint32_t* colmax = reinterpret_cast<uint32_t*>(smem + L::OFF_COL);
-  uint2* cand = reinterpret_cast<uint2*>(smem + L::OFF_CAND);
-  int* ccount = reinterpret_cast<int*>(smem + L::OFF_CCOUNT);
+  uint2* lst = reinterpret_cast<uint2*>(smem + L::OFF_LIST);
+  int* lcount = reinterpret_cast<int*>(smem + L::OFF_LCOUNT);
   uint32_t* runmax = reinterpret_cast<uint32_t*>(smem + L::OFF_RUNMAX);
   unsigned long long* best = reinterpret_cast<unsigned long long*>(smem + L::OFF_BEST);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -515,7 +554,7 @@ __device__ __forceinline__ bool mma_tile(const UnitState& us, uint8_t* smem, Mma
     return o;
   };
   auto seg_valid = [&](int l, int s) { return ((t0 >> l) + s + 1) << l <= nv; };
-  // GEMM windows (2..32) present; sigma numbers their segments in
+  // GEMM windows (4..32) present; sigma numbers their segments in
   // ascending window order
   const uint32_t gmask = (uint32_t)win_mask & kGemmMask;
   const int nG = __popc(gmask);
@@ -531,9 +570,12 @@ __device__ __forceinline__ bool mma_tile(const UnitState& us, uint8_t* smem, Mma
     }
   auto gwin = [&](int i) { return (int)((gl >> (3 * i)) & 7u); };
   auto sig_base = [&](int l) { return (int)((sb >> (5 * l)) & 31u); };
-  const int njobs = NMB * nG;
 
+  int* piece_next = reinterpret_cast<int*>(smem + L::OFF_PIECE);
+  for (int i = tid; i < kMaxSegPerTile; i += NT) best[i] = 0ull;
+  if (tid == 0) *piece_next = 0;
   float scale = 1.f;
+  if (nG == 0) __syncthreads();
   if (nG > 0) {
     if constexpr (PREC != VOLKS_BF16) {
       // per-tile power-of-two operand scale: largest |component| -> < 2^SCALE_EXP
@@ -553,10 +595,9 @@ __device__ __forceinline__ bool mma_tile(const UnitState& us, uint8_t* smem, Mma
       }
     }
     pack_a<LD, PREC>(S, A, 0, scale, tid, NT);
-    if (NMB > 1) pack_a<LD, PREC>(S, A + O::A_BYTES, 1, scale, tid, NT);
-    for (int i = tid; i < nsig * kMRows; i += NT) colmax[i] = 0u;
+    pack_a<LD, PREC>(S, A + O::A_BYTES, 1, scale, tid, NT);
     for (int i = tid; i < nsig; i += NT) {
-      ccount[i] = 0;
+      lcount[i] = 0;
       runmax[i] = 0u;
     }
     tc::fence_async_smem();
@@ -564,137 +605,184 @@ __device__ __forceinline__ bool mma_tile(const UnitState& us, uint8_t* smem, Mma
     __syncthreads();
   }
 
-  bool ok = true;
-  if (warp == 0) {
-    // ---- producer: issue every job as its TMEM buffer and A block are ready ----
-    if (lane == 0) {
-      int j = 0;
-      for (int b = 0; ok && nG > 0 && b < NMB; ++b) {
-        if (b >= 2) {
-          ok = tc::mbar_wait_bounded(&bars.afull[b & 1], cx.a_par[b & 1], kWaitCycles);
-          cx.a_par[b & 1] ^= 1u;
+  // ---- the exact 1- and 2-AP windows as a pool of work pieces ----
+  // The helper warps take pieces while the barrier they wait on is not yet
+  // complete, and after their own work: piece p < n1p is a 1-AP segment, the
+  // next n2p are halves of 2-AP segments; each ends in one 64-bit atomicMax
+  // into the segment's key, so the order of the pieces does not matter.
+  const int n1p = (win_mask & 1) ? kTile : 0;
+  const int n2p = (win_mask & 2) ? kTile : 0;
+  auto piece = [&]() -> bool {
+    int pc = 0;
+    if (lane == 0) pc = atomicAdd(piece_next, 1);
+    pc = __shfl_sync(0xffffffffu, pc, 0);
+    if (pc >= n1p + n2p) return false;
+    if (pc < n1p) {
+      const int s = pc;
+      if (!seg_valid(0, s)) return true;
+      float bp = -1.f;
+      int bc = 0;
+#pragma unroll 4
+      for (int jj = 0; jj < N1; ++jj) {
+        const int c = lane + 32 * jj;
+        const float pw = cabs2(S[s * LD + c]);
+        if (pw > bp) {
+          bp = pw;
+          bc = c;
         }
-        const uint32_t a_addr = tc::smem_u32(A + (b & 1) * O::A_BYTES);
+      }
+      const unsigned long long key = warp_key(bp, (uint32_t)(bc * P + r));
+      if (lane == 0) atomicMax(best + slot_base(0) + s, key);
+    } else {
+      // 2-AP segment s, columns of half h: each column's largest rate cell
+      // is r0 + max(|2 rx|, |2 ry|, |sqrt2 (rx + ry)|, |sqrt2 (ry - rx)|),
+      // which equals the largest of the eight cells rate_cells_w2 gives
+      // (rounding is monotonic); the lane's best column (the first on equal
+      // powers) is then resolved to its cell once.
+      const int q = pc - n1p, s = q >> 1, h = q & 1;
+      if (!seg_valid(1, s)) return true;
+      const float2* y0p = S + (2 * s) * LD;
+      const float2* y1p = y0p + LD;
+      float bp = -1.f;
+      int bc = lane + 32 * h * (N1 / 2);
+#pragma unroll 4
+      for (int jj = h * (N1 / 2); jj < (h + 1) * (N1 / 2); ++jj) {
+        const int c = lane + 32 * jj;
+        const float2 y0 = y0p[c], y1 = y1p[c];
+        const float r0 = fmaf(y1.y, y1.y, fmaf(y1.x, y1.x, cabs2(y0)));
+        const float rx = fmaf(y1.y, y0.y, y1.x * y0.x);
+        const float ry = fmaf(y1.y, y0.x, -(y1.x * y0.y));
+        constexpr float kS2 = Tw<8, 1>::re * 2.0f;
+        const float a = rx + rx, bb = ry + ry;
+        const float cc = kS2 * (rx + ry), dd = kS2 * (ry - rx);
+        const float pm = r0 + tc::fmax3(fabsf(a), fabsf(bb), fmaxf(fabsf(cc), fabsf(dd)));
+        if (pm > bp) {
+          bp = pm;
+          bc = c;
+        }
+      }
+      float P8[8];
+      rate_cells_w2(y0p[bc], y1p[bc], P8);
+      float pv;
+      uint32_t qv;
+      argmax_tree<0, 8>([&](auto qq) { return P8[decltype(qq)::value]; }, pv, qv);
+      const unsigned long long key = warp_key(pv, qv * M + (uint32_t)(bc * P + r));
+      if (lane == 0) atomicMax(best + slot_base(1) + s, key);
+    }
+    return true;
+  };
+
+  bool ok = true;
+  const bool drain = warp >= 4 && warp < 4 + 4 * NWG;
+  if (warp == 0) {
+    // ---- issuing thread ----
+    if (lane == 0 && nG > 0) {
+      int j = 0;
+      for (int b = 0; ok && b < NMB; ++b) {
+        if (b >= 2) {
+          ok = tc::mbar_wait_bounded(&bars.afull[b & 1], pbit(cx.par, PB_AFULL + (b & 1)), kWaitCycles);
+          cx.par ^= 1u << (PB_AFULL + (b & 1));
+        }
         for (int gi = 0; ok && gi < nG; ++gi, ++j) {
           const int buf = j & 1, l = gwin(gi);
-          if (cx.n_use[buf] > 0)
-            ok = tc::mbar_wait_bounded(&bars.empty[buf], (cx.n_use[buf] - 1u) & 1u, kWaitCycles);
+          const uint32_t nu = buf ? cx.n_use1 : cx.n_use0;
+          if (nu > 0) ok = tc::mbar_wait_bounded(&bars.empty[buf], (nu - 1u) & 1u, kWaitCycles);
           if (!ok) break;
           tc::fence_after_sync();
-          issue_ops<PREC>(jt.ops[l], jt.n_ops[l], tc::sdesc_sw(a_addr, O::A_ROW),
-                          tc::sdesc_sw(tc::smem_u32(Bm + O::b_off(l)), (uint32_t)O::b_row_bytes(l)),
-                          cx.tmem + (uint32_t)buf * kJobCols);
+          const uint64_t ad = jt.ad[b & 1], bd = jt.bd[l];
+          const uint32_t d = cx.tmem + (uint32_t)buf * kJobCols;
+          // straight-line MMAs with compile-time operand offsets
+          switch (l) {
+            case 2: issue_window_t<PREC, 2>(ad, bd, d); break;
+            case 3: issue_window_t<PREC, 3>(ad, bd, d); break;
+            case 4: issue_window_t<PREC, 4>(ad, bd, d); break;
+            default: issue_window_t<PREC, 5>(ad, bd, d); break;
+          }
           tc::mma_commit(&bars.full[buf]);
-          ++cx.n_use[buf];
+          if (buf) ++cx.n_use1; else ++cx.n_use0;
         }
+        // A buffer b & 1 is free once these MMAs complete
+        if (ok && b + 2 < NMB) tc::mma_commit(&bars.adone[b & 1]);
       }
     }
     __syncwarp();
-  } else {
-    // ---- consumers: exact windows while the first MMAs run ----
-    if (win_mask & 1) {
-      for (int s = warp - 1; s < kTile; s += NC) {
-        if (!seg_valid(0, s)) continue;
-        float bp = -1.f;
-        int bc = 0;
-#pragma unroll 4
-        for (int j = 0; j < N1; ++j) {
-          const int c = lane + 32 * j;
-          const float p = cabs2(S[s * LD + c]);
-          if (p > bp) {
-            bp = p;
-            bc = c;
-          }
-        }
-        const unsigned long long key = warp_key(bp, (uint32_t)(bc * P + r));
-        if (lane == 0) best[slot_base(0) + s] = key;
+    if (nG == 0)
+      while (piece()) {
       }
-    }
-    if (win_mask & 2) {
-      for (int s = warp - 1; s < kTile / 2; s += NC) {
-        if (!seg_valid(1, s)) continue;
-        float bp = -1.f;
-        uint32_t bl = 0xffffffffu;
-#pragma unroll 2
-        for (int j = 0; j < N1; ++j) {
-          const int c = lane + 32 * j;
-          float P8[8];
-          rate_cells_w2(S[(2 * s) * LD + c], S[(2 * s + 1) * LD + c], P8);
-          float pv;
-          uint32_t qv;
-          argmax_tree<0, 8>([&](auto qq) { return P8[decltype(qq)::value]; }, pv, qv);
-          const uint32_t lin = qv * M + (uint32_t)(c * P + r);
-          if (pv > bp || (pv == bp && lin < bl)) {
-            bp = pv;
-            bl = lin;
-          }
-        }
-        const unsigned long long key = warp_key(bp, bl);
-        if (lane == 0) best[slot_base(1) + s] = key;
-      }
-    }
-    // ---- consumers: drain each job's accumulators ----
-    const int q = warp & 3;
-    const int cnt = NW / 4 - (q == 0 ? 1 : 0);           // consumer warps of lane quarter q
-    const int k = (warp >> 2) - (q == 0 ? 1 : 0);
-    const int ch0 = (k * 8) / cnt, ch1 = ((k + 1) * 8) / cnt;  // 32-column chunks of this warp
-    const int row = q * 32 + lane;
-    int j = 0;
+  } else if (drain) {
+    // ---- drain warpgroups: whole jobs, 32 TMEM lanes per warp ----
+    if (nG > 0) {
+      const int q = warp & 3, wg = (warp - 4) >> 2;
+      const int row = q * 32 + lane;
+      int j = 0;
 #pragma unroll 1
-    for (int b = 0; b < NMB; ++b) {
-#pragma unroll 1
-      for (int gi = 0; gi < nG; ++gi, ++j) {
-        const int buf = j & 1, l = gwin(gi);
-        const bool last = gi == nG - 1;
-        // after a failed wait the warp keeps walking the loop (no more waits,
-        // no TMEM reads) so that every barrier below is still reached
-        // one lane per warp waits (the others idle at the shuffle)
-        if (ok) {
-          bool w_ok = true;
-          if (lane == 0) w_ok = tc::mbar_wait_bounded(&bars.full[buf], cx.f_par[buf], kWaitCycles);
-          ok = __shfl_sync(0xffffffffu, w_ok, 0);
+      for (int b = 0; b < NMB; ++b) {
+        uint32_t* cmb = colmax + (size_t)(b & 1) * kGemmSegs * kMRows + row;
+        if (b >= 2) {
+          // the helpers have merged block b - 2 out of this buffer
+          if (ok) ok = warp_wait(&bars.cfree[b & 1], pbit(cx.par, PB_CFREE + (b & 1)), lane);
+          cx.par ^= 1u << (PB_CFREE + (b & 1));
         }
-        cx.f_par[buf] ^= 1u;
-        tc::fence_after_sync();
-        if (last && b + 2 < NMB) {
-          // every MMA reading A block b has completed: refill its buffer with block b + 2
+#pragma unroll 1
+        for (int gi = 0; gi < nG; ++gi, ++j) {
+          const int buf = j & 1, l = gwin(gi);
+          if (NWG == 2 && buf != wg) continue;
+          if (ok) ok = warp_wait(&bars.full[buf], pbit(cx.par, PB_FULL + buf), lane);
+          cx.par ^= 1u << (PB_FULL + buf);
+          tc::fence_after_sync();
+          const uint32_t tb = cx.tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * kJobCols;
+          uint32_t* cm = cmb + sig_base(l) * kMRows;
           if (ok) {
-            pack_a<LD, PREC>(S, A + (b & 1) * O::A_BYTES, b + 2, scale, tid - 32, NT - 32);
+            switch (l) {
+              case 2: drain_job<2>(tb, cm, &bars.empty[buf], lane); break;
+              case 3: drain_job<3>(tb, cm, &bars.empty[buf], lane); break;
+              case 4: drain_job<4>(tb, cm, &bars.empty[buf], lane); break;
+              default: drain_job<5>(tb, cm, &bars.empty[buf], lane); break;
+            }
+          } else {
+            // after a failed wait: no TMEM reads, but every arrival still happens
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bars.empty[buf]);
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bars.cdone[b & 1]);
+      }
+    }
+  } else {
+    // ---- helper warps ----
+    const int hw = warp < 4 ? warp - 1 : warp - 4 - 4 * NWG + 3;
+    if (nG > 0) {
+#pragma unroll 1
+      for (int b = 0; b < NMB; ++b) {
+        if (b + 2 < NMB) {
+          // refill A buffer b & 1 with block b + 2 once its MMAs are done
+          if (ok) ok = warp_wait_busy(&bars.adone[b & 1], pbit(cx.par, PB_ADONE + (b & 1)), lane, piece);
+          cx.par ^= 1u << (PB_ADONE + (b & 1));
+          if (ok) {
+            pack_a<LD, PREC>(S, A + (b & 1) * O::A_BYTES, b + 2, scale, hw * 32 + lane, NHELP * 32);
             tc::fence_async_smem();
           }
           __syncwarp();
           if (lane == 0) mbar_arrive(&bars.afull[b & 1]);
         }
-        const uint32_t tb = cx.tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * kJobCols;
-        uint32_t* cm = colmax + sig_base(l) * kMRows + row;
+        if (ok) ok = warp_wait_busy(&bars.cdone[b & 1], pbit(cx.par, PB_CDONE + (b & 1)), lane, piece);
+        cx.par ^= 1u << (PB_CDONE + (b & 1));
         if (ok) {
-          switch (l) {
-            case 2: drain_job<2>(tb, cm, ch0, ch1, &bars.empty[buf], lane); break;
-            case 3: drain_job<3>(tb, cm, ch0, ch1, &bars.empty[buf], lane); break;
-            case 4: drain_job<4>(tb, cm, ch0, ch1, &bars.empty[buf], lane); break;
-            default: drain_job<5>(tb, cm, ch0, ch1, &bars.empty[buf], lane); break;
-          }
-        } else {
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&bars.empty[buf]);
+          // the same warp merges a segment in every block, so blocks stay in order
+          const uint32_t* cmb = colmax + (size_t)(b & 1) * kGemmSegs * kMRows;
+          for (int sg = hw; sg < nsig; sg += NHELP)
+            merge_block<PREC>(cmb + sg * kMRows, b, lst, lcount, runmax, sg, lane);
         }
-        if (last) {
-          // M-block b complete: merge its cells into every segment's candidates
-          consumer_sync<NT - 32>();
-          for (int sg = warp - 1; sg < nsig; sg += NC) {
-            uint32_t v[4], c[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              v[i] = colmax[sg * kMRows + lane + 32 * i];
-              c[i] = (uint32_t)(b * kMRows + lane + 32 * i);
-              colmax[sg * kMRows + lane + 32 * i] = 0u;
-            }
-            merge_block<PREC>(v, c, cand, ccount, runmax, sg, lane);
-          }
-          consumer_sync<NT - 32>();
+        if (b + 2 < NMB) {
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&bars.cfree[b & 1]);
         }
       }
     }
+    if (ok)
+      while (piece()) {
+      }
   }
   if (__syncthreads_or(!ok)) {
     if (tid == 0) atomicOr(err, 1u);
@@ -709,9 +797,10 @@ __device__ __forceinline__ bool mma_tile(const UnitState& us, uint8_t* smem, Mma
         if (sg >= sig_base(gwin(i))) l = gwin(i);
       const int s = sg - sig_base(l);
       if (!seg_valid(l, s)) continue;
+      const int nc = finish_list<PREC>(lst, lcount, runmax, sg, lane);
       int ci = lane >> 2;
-      if (ci >= ccount[sg]) ci = 0;
-      const int c = (int)cand[sg * kTopK + ci].y;
+      if (ci >= nc) ci = 0;
+      const int c = (int)lst[sg * kList + ci].y;
       const int rho = lane & 3;
       float pw;
       uint32_t qq;
@@ -761,13 +850,23 @@ __global__ void __launch_bounds__(32 * N1, 1) search_mma_kernel(const __grid_con
   __shared__ float s_amax;
   const int tid = threadIdx.x;
   using L = MmaSmem<N1, PREC>;
-  build_rate_dft<PREC>(smem + L::OFF_B, p.d[0].tw_m, p.d[0].M, tid, N);
+  build_rate_dft<PREC, 2>(smem + L::OFF_B, p.d[0].tw_m, p.d[0].M, tid, N);
   if (tid == 0) {
-    for (int l = 1; l <= 5; ++l) jt.n_ops[l] = job_ops<PREC>(l, jt.ops[l]);
+    constexpr int NWG = N1 >= 16 ? 2 : 1, NHELP = N1 - 1 - 4 * NWG;
+    for (int l = 1; l <= 5; ++l) {
+      jt.n_ops[l] = job_ops<PREC>(l, jt.ops[l]);
+      if (l >= 2)
+        jt.bd[l] = tc::sdesc_sw(tc::smem_u32(smem + L::OFF_B + Op<PREC>::b_off(l) - Op<PREC>::b_off(2)),
+                              (uint32_t)Op<PREC>::b_row_bytes(l));
+    }
     for (int i = 0; i < 2; ++i) {
+      jt.ad[i] = tc::sdesc_sw(tc::smem_u32(smem + L::OFF_A + i * Op<PREC>::A_BYTES), Op<PREC>::A_ROW);
       tc::mbar_init(&bars.full[i], 1);
-      tc::mbar_init(&bars.empty[i], N1 - 1);
-      tc::mbar_init(&bars.afull[i], N1 - 1);
+      tc::mbar_init(&bars.empty[i], 4);
+      tc::mbar_init(&bars.afull[i], NHELP);
+      tc::mbar_init(&bars.adone[i], 1);
+      tc::mbar_init(&bars.cdone[i], 4 * NWG);
+      tc::mbar_init(&bars.cfree[i], NHELP);
     }
     tc::mbar_init_fence();
   }
@@ -781,9 +880,8 @@ __global__ void __launch_bounds__(32 * N1, 1) search_mma_kernel(const __grid_con
   tc::fence_after_sync();
   MmaCtx cx;
   cx.tmem = s_tmem;
-  cx.f_par[0] = cx.f_par[1] = 0u;
-  cx.n_use[0] = cx.n_use[1] = 0u;
-  cx.a_par[0] = cx.a_par[1] = 0u;
+  cx.par = 0u;
+  cx.n_use0 = cx.n_use1 = 0u;
   for (;;) {
     if (tid == 0) {
       const long long u = (long long)atomicAdd(p.counter, 1ULL);
