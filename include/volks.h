@@ -589,12 +589,12 @@ int volks_localize(const volks_loc_obs *obs, int32_t n, const volks_loc_params *
  * exceeds VOLKS_NOALLOC_SCRATCH_BYTES, for two polarisation products or
  * auto spectra (one product, cross-spectrum normalisation only), or for
  * the descriptors volks_search_segment rejects; VOLKS_ECUDA if a launch
- * fails.  Returns
- * without waiting for the device.
+ * fails.  Returns without waiting for the device.
  *
  * All calls on a device share the one scratch array, which keeps the
- * previous call's contents; each call clears what must start at zero on
- * its own stream.  Calls that overlap on the GPU (different streams or
+ * previous call's contents; every part of it that a call reads is first
+ * written by that call on its own stream (no part needs to start at zero,
+ * so nothing is cleared).  Calls that overlap on the GPU (different streams or
  * host threads) race on the array and must be serialised by the caller.
  * The first call on each device looks up the array's device address with
  * that device current; make that first call before any stream capture.

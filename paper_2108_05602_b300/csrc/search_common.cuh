@@ -127,7 +127,46 @@ struct UnitState {
   int b, d, r, t0, nv, valid;
 };
 
-// One work unit = (baseline b, DM trial d, 32-AP tile, delay residue r).
+// Segment of slot i of a tile (slots of the searched windows in ascending
+// window order): its window log2 l and its index sg in the (b, DM, window)
+// series, or false if the segment is not complete within the nv valid APs.
+template <bool SLIDE>
+__device__ __forceinline__ bool slot_segment(int i, int win_mask, int desc_mask, int t0, int nv, int& l, int& sg) {
+  int base = 0;
+  for (l = 0;; ++l) {
+    if (!(win_mask & (1 << l))) continue;
+    if (i < base + (kTile >> l)) break;
+    base += kTile >> l;
+  }
+  const int s = i - base;
+  const int W = 1 << l;
+  if constexpr (SLIDE) {
+    const int start = t0 + s * W;
+    if (start + W > nv) return false;
+    sg = desc_slide(desc_mask) ? start : start >> l;
+  } else {
+    sg = t0 / W + s;
+    if ((sg + 1) * W > nv) return false;
+  }
+  return true;
+}
+
+// Store the tile's final keys (largest over its delay residues) once.
+template <bool SLIDE>
+__device__ __forceinline__ void store_keys(const UnitState& us, const unsigned long long* run, int win_mask) {
+  int ns = 0;
+  for (int l = 0; l <= kMaxWinLog; ++l)
+    if (win_mask & (1 << l)) ns += kTile >> l;
+  unsigned long long* keys = us.a.keys + ((size_t)us.b * us.a.n_dm + us.d) * us.a.seg_per_bd;
+  for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+    int l, sg;
+    if (slot_segment<SLIDE>(i, win_mask, us.a.win_mask, us.t0, us.nv, l, sg)) keys[us.a.win_off_l[l] + sg] = run[i];
+  }
+}
+
+
+// One pass of a work unit (baseline b, DM trial d, 32-AP tile) per delay
+// residue r.
 // Zero padding by pad_delay, with the band folded FOLD times, splits the
 // M-point delay transform (M = pad_delay * n_f) into P = pad_delay * FOLD
 // independent N-point FFTs, N = n_f / FOLD:

@@ -28,7 +28,7 @@ __device__ __forceinline__ int sliding_windows(int win_mask, int t0) {
 }
 
 template <int N1, int PADR, int FOLD, bool SLIDE>
-__device__ __forceinline__ void search_tile(const UnitState& us, float2* S, uint2* slot) {
+__device__ __forceinline__ void search_tile(const UnitState& us, float2* S, uint2* slot, unsigned long long* run) {
   constexpr int N = 32 * N1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   delay_stage<N1, FOLD>(us, S);
@@ -56,29 +56,11 @@ __device__ __forceinline__ void search_tile(const UnitState& us, float2* S, uint
     if (win_mask & 32) rate_window<32, PADR, N1, SLIDE>(S, c, m, M, t0, nv, slot_base(5), slot, warp, lane);
   }
   __syncthreads();
-  // ---- merge the warps' bests and publish one key per segment ----
+  // ---- merge the warps' bests into the tile's running key of each segment ----
   const int ns = slot_base(kMaxWinLog + 1);
-  const int t0 = us.t0, nv = us.nv;
-  unsigned long long* keys =
-      us.a.keys + ((size_t)us.b * us.a.n_dm + us.d) * us.a.seg_per_bd;
   for (int i = threadIdx.x; i < ns; i += N) {
-    int l = 0, base = 0;
-    for (;; ++l) {
-      if (!(win_mask & (1 << l))) continue;
-      if (i < base + (kTile >> l)) break;
-      base += kTile >> l;
-    }
-    const int s = i - base;
-    const int W = 1 << l;
-    int sg;
-    if constexpr (SLIDE) {
-      const int start = t0 + s * W;
-      if (start + W > nv) continue;
-      sg = desc_slide(us.a.win_mask) ? start : start >> l;
-    } else {
-      sg = t0 / W + s;
-      if ((sg + 1) * W > nv) continue;
-    }
+    int l, sg;
+    if (!slot_segment<SLIDE>(i, win_mask, us.a.win_mask, us.t0, us.nv, l, sg)) continue;
     uint32_t bp = 0, bl = 0xffffffffu;
 #pragma unroll 4
     for (int w = 0; w < N1; ++w) {
@@ -89,13 +71,15 @@ __device__ __forceinline__ void search_tile(const UnitState& us, float2* S, uint
       }
     }
     const unsigned long long key = ((unsigned long long)bp << 32) | (unsigned long long)(0xffffffffu - bl);
-    atomicMax(keys + us.a.win_off_l[l] + sg, key);
+    run[i] = max(run[i], key);
   }
 }
 
-// Search kernel over the ranges of a Batch: one unit per CTA, or
-// persistent CTAs pulling units from an atomic counter (dynamic load
-// balancing across ranges of different sizes).
+// Search kernel over the ranges of a Batch: one unit (baseline, DM trial,
+// 32-AP tile) per CTA, or persistent CTAs pulling units from an atomic
+// counter (dynamic load balancing across ranges of different sizes).  A
+// unit runs every delay residue of its tile in turn and keeps each
+// segment's best key in shared memory, so each key is stored once.
 template <int N1, int PADR, int FOLD, bool SLIDE>
 __global__ void __launch_bounds__(32 * N1, 16 / N1) search_kernel(const __grid_constant__ Batch p) {
   constexpr int N = 32 * N1;
@@ -105,6 +89,7 @@ __global__ void __launch_bounds__(32 * N1, 16 / N1) search_kernel(const __grid_c
   __shared__ UnitState us;
   __shared__ int s_desc;
   __shared__ long long s_unit;
+  __shared__ unsigned long long run[kMaxSegPerTile];
   const bool persistent = p.counter != nullptr;
   long long next = (long long)blockIdx.x + p.unit0;
   for (;;) {
@@ -125,9 +110,6 @@ __global__ void __launch_bounds__(32 * N1, 16 / N1) search_kernel(const __grid_c
     if (threadIdx.x == 0) {
       const SegDesc& a = p.d[di];
       long long unit = s_unit - a.base;
-      const int P = a.pad_delay * FOLD;
-      us.r = (int)(unit % P);
-      unit /= P;
       // sliding segments: a search of every window w back to back from AP
       // phase phi < w, for each phase (the unit searches the windows wider
       // than its phase)
@@ -145,7 +127,18 @@ __global__ void __launch_bounds__(32 * N1, 16 / N1) search_kernel(const __grid_c
       us.valid = us.t0 < us.nv && (!SLIDE || sliding_windows(a.win_mask, us.t0) != 0);
     }
     __syncthreads();
-    if (us.valid) search_tile<N1, PADR, FOLD, SLIDE>(us, S, slot);
+    if (us.valid) {
+      const int P = us.a.pad_delay * FOLD;
+      const int win_mask = SLIDE ? sliding_windows(us.a.win_mask, us.t0) : us.a.win_mask;
+      for (int i = threadIdx.x; i < kMaxSegPerTile; i += N) run[i] = 0ull;
+      for (int r = 0; r < P; ++r) {
+        if (threadIdx.x == 0) us.r = r;
+        __syncthreads();
+        search_tile<N1, PADR, FOLD, SLIDE>(us, S, slot, run);
+        __syncthreads();
+      }
+      store_keys<SLIDE>(us, run, win_mask);
+    }
     if (!persistent) return;
     __syncthreads();
   }

@@ -564,11 +564,11 @@ int volks_search_segment(const volks_segment* seg, const volks_params* prm, void
     release(r);
     return rc;
   }
-  VK_TRY(cudaMemsetAsync(j.d_keys, 0, j.keys_bytes_per_dm() * j.dm_chunk, st), "memset peaks");
   VK_TRY(j.enqueue_prep(st, &r->n_launch), "prep kernels");
   VK_TRY(cudaEventRecord(r->ev[2], st), "event");
 
-  // a4-a7: persistent CTAs over the segment's (baseline, DM, tile, residue) units
+  // a4-a7: persistent CTAs over the segment's (baseline, DM, tile) units; every
+  // valid segment's key is stored once, so the key buffer needs no clearing
   int fold = 0;
   if (const char* f = std::getenv("VOLKS_SEARCH_FOLD")) fold = std::atoi(f);
   const vk::SearchVariant v = vk::default_variant(j.n_f, j.prec, fold);

@@ -200,8 +200,11 @@ SearchVariant default_variant(int n_f, int precision, int fold_override) {
   return best;
 }
 
+// Work units of a range: (baseline, DM trial, 32-AP tile[, AP phase]); a
+// unit runs all pad_delay x fold delay residues of its tile.
 long long search_units(const SegDesc& d, SearchVariant v) {
-  return (long long)d.n_bl * d.n_tiles * d.n_dm * d.pad_delay * v.fold * desc_phases(d.win_mask);
+  (void)v;
+  return (long long)d.n_bl * d.n_tiles * d.n_dm * desc_phases(d.win_mask);
 }
 
 int search_occupancy(SearchVariant v, int pad_rate, int precision) {
@@ -279,23 +282,28 @@ __device__ __forceinline__ double seg_z(double rho, double mu, double inv_sd) {
 }
 
 template <int NT>
-__device__ __forceinline__ double block_sum(double v, double* red) {
-  red[threadIdx.x] = v;
+__device__ __forceinline__ double2 block_sum2(double a, double b, double2* red) {
+  red[threadIdx.x] = make_double2(a, b);
   __syncthreads();
 #pragma unroll
   for (int h = NT / 2; h > 0; h >>= 1) {
-    if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    if ((int)threadIdx.x < h) {
+      const double2 x = red[threadIdx.x], y = red[threadIdx.x + h];
+      red[threadIdx.x] = make_double2(x.x + y.x, x.y + y.y);
+    }
     __syncthreads();
   }
-  const double r = red[0];
+  const double2 r = red[0];
   __syncthreads();
   return r;
 }
 
-// One CTA per (range, baseline, DM trial, window) series.
+// One CTA per (range, baseline, DM trial, window) series: FP64 mean and
+// population standard deviation of rho (one read of the keys), then the
+// z >= thresh bitmap (a second read).
 __global__ void __launch_bounds__(256) select_kernel(const __grid_constant__ Batch p) {
   constexpr int NT = 256;
-  __shared__ double red[NT];
+  __shared__ double2 red2[NT];
   const long long u = (long long)blockIdx.x + p.unit0;
   if (u >= p.total) return;
   const SegDesc& a = p.d[find_desc(p, u)];
@@ -309,15 +317,23 @@ __global__ void __launch_bounds__(256) select_kernel(const __grid_constant__ Bat
   const double inv_wn = seg_inv_wn(W, a.n_eff);
   const size_t bd = (size_t)b * a.n_dm + d;
   const unsigned long long* k = a.keys + bd * a.seg_per_bd + a.win_off[wi];
-  double s = 0.0;
-  for (int i = threadIdx.x; i < nseg; i += NT) s += seg_rho(k[i], inv_wn);
-  const double mu = nseg > 0 ? block_sum<NT>(s, red) / (double)nseg : 0.0;
-  double ss = 0.0;
+  // one pass over the keys: sums of (rho - K) and (rho - K)^2 about the
+  // series' first value K (the shift keeps the variance free of
+  // cancellation), combined in a fixed tree
+  const double K = nseg > 0 ? seg_rho(k[0], inv_wn) : 0.0;
+  double s1 = 0.0, s2 = 0.0;
   for (int i = threadIdx.x; i < nseg; i += NT) {
-    const double dv = seg_rho(k[i], inv_wn) - mu;
-    ss = fma(dv, dv, ss);
+    const double dv = seg_rho(k[i], inv_wn) - K;
+    s1 += dv;
+    s2 = fma(dv, dv, s2);
   }
-  const double sd = nseg > 0 ? sqrt(block_sum<NT>(ss, red) / (double)nseg) : 0.0;
+  double mu = 0.0, sd = 0.0;
+  if (nseg > 0) {
+    const double2 t = block_sum2<NT>(s1, s2, red2);
+    const double n = (double)nseg, m1 = t.x / n;
+    mu = K + m1;
+    sd = sqrt(fmax(t.y / n - m1 * m1, 0.0));
+  }
   if (threadIdx.x == 0) {
     double* st = a.stats + (((size_t)b * a.n_dm_total + a.d0 + d) * a.n_win + wi) * 2;
     st[0] = mu;

@@ -524,7 +524,8 @@ __device__ __forceinline__ int finish_list(uint2* lst, const int* lcount, const 
 //                    block (once every drain warp passed `cdone`).
 template <int N1, int FOLD, int PREC>
 __device__ __forceinline__ bool mma_tile(const UnitState& us, uint8_t* smem, MmaCtx& cx, MmaBars& bars,
-                                         const JobTable& jt, float* s_amax, unsigned int* err) {
+                                         const JobTable& jt, float* s_amax, unsigned int* err,
+                                         unsigned long long* run) {
   using O = Op<PREC>;
   using L = MmaSmem<N1, PREC>;
   constexpr int N = 32 * N1, LD = N + 1, NT = N, NW = N1, NMB = N / kMRows;
@@ -817,21 +818,9 @@ __device__ __forceinline__ bool mma_tile(const UnitState& us, uint8_t* smem, Mma
     }
   }
   __syncthreads();
-  // ---- publish one key per valid segment ----
+  // ---- fold this residue's keys into the tile's running keys ----
   const int ns = slot_base(kMaxWinLog + 1);
-  unsigned long long* keys = us.a.keys + ((size_t)us.b * us.a.n_dm + us.d) * us.a.seg_per_bd;
-  for (int i = tid; i < ns; i += NT) {
-    int l = 0, base = 0;
-    for (;; ++l) {
-      if (!(win_mask & (1 << l))) continue;
-      if (i < base + (kTile >> l)) break;
-      base += kTile >> l;
-    }
-    const int s = i - base;
-    const int sg = (t0 >> l) + s;
-    if ((sg + 1) << l > nv) continue;
-    atomicMax(keys + us.a.win_off_l[l] + sg, best[i]);
-  }
+  for (int i = tid; i < ns; i += NT) run[i] = max(run[i], best[i]);
   return true;
 }
 
@@ -848,6 +837,7 @@ __global__ void __launch_bounds__(32 * N1, 1) search_mma_kernel(const __grid_con
   __shared__ __align__(8) JobTable jt;
   __shared__ uint32_t s_tmem;
   __shared__ float s_amax;
+  __shared__ unsigned long long run[kMaxSegPerTile];
   const int tid = threadIdx.x;
   using L = MmaSmem<N1, PREC>;
   build_rate_dft<PREC, 2>(smem + L::OFF_B, p.d[0].tw_m, p.d[0].M, tid, N);
@@ -900,9 +890,6 @@ __global__ void __launch_bounds__(32 * N1, 1) search_mma_kernel(const __grid_con
     if (tid == 0) {
       const SegDesc& a = p.d[di];
       long long unit = s_unit - a.base;
-      const int P = a.pad_delay * FOLD;
-      us.r = (int)(unit % P);
-      unit /= P;
       us.d = (int)(unit % a.n_dm);
       unit /= a.n_dm;
       const int tile = (int)(unit % a.n_tiles);
@@ -912,7 +899,23 @@ __global__ void __launch_bounds__(32 * N1, 1) search_mma_kernel(const __grid_con
       us.valid = us.t0 < us.nv;
     }
     __syncthreads();
-    if (us.valid && !mma_tile<N1, FOLD, PREC>(us, smem, cx, bars, jt, &s_amax, p.err)) break;
+    if (us.valid) {
+      // every delay residue of the tile in turn; each key is stored once
+      const int P = us.a.pad_delay * FOLD;
+      for (int i = tid; i < kMaxSegPerTile; i += N) run[i] = 0ull;
+      bool failed = false;
+      for (int r = 0; r < P && !failed; ++r) {
+        if (tid == 0) {
+          us.r = r;
+          s_amax = 0.f;
+        }
+        __syncthreads();
+        failed = !mma_tile<N1, FOLD, PREC>(us, smem, cx, bars, jt, &s_amax, p.err, run);
+        __syncthreads();
+      }
+      if (failed) break;
+      store_keys<false>(us, run, us.a.win_mask);
+    }
     __syncthreads();
   }
   tc::fence_before_sync();

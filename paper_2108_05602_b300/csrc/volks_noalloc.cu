@@ -15,9 +15,10 @@
 //    device that loads this library until the process exits;
 //  * larger problems are rejected with VOLKS_EINVAL (nothing is launched);
 //  * all calls on a device share the array and it keeps the previous
-//    call's contents; the parts that must start at zero are cleared on the
-//    call's stream.  Calls that overlap on the GPU (other streams, other
-//    host threads) race on the array: serialise them;
+//    call's contents; every part a call reads is first written by that
+//    call on its stream, so nothing needs clearing.  Calls that overlap on
+//    the GPU (other streams, other host threads) race on the array:
+//    serialise them;
 //  * the first call on each device looks up the array's device address
 //    with cudaGetSymbolAddress (with that device current); make that first
 //    call before any stream capture.
@@ -349,10 +350,9 @@ extern "C" int volks_search_peaks_noalloc(const volks_segment* seg, const volks_
   pa.skip_first_chan = prm->skip_first_chan;
   if ((rc = cu(vk::launch_prep(pa, st, &n_launch), "prep kernels"))) return rc;
 
-  // the peaks are combined with atomicMax: they must start at zero
+  // every valid segment's key is stored once by the search (the unpack
+  // kernel reads only those), so the keys need no clearing
   unsigned long long* keys = reinterpret_cast<unsigned long long*>(sp + o_keys);
-  if ((rc = cu(cudaMemsetAsync(keys, 0, (size_t)total * sizeof(unsigned long long), st), "clear peaks")))
-    return rc;
   vk::SearchArgs sa{};
   sa.xn = pa.xn;
   sa.shifts = ta.shifts;

@@ -148,12 +148,8 @@ int enqueue_all(volks_plan* p, cudaStream_t s) {
     auto classes = round_classes(p, c);
     std::vector<RangeRef> all;
     for (auto& kv : classes) {
-      for (auto& r : kv.second) {
-        all.push_back(r);
-        const vk::SegDesc d = r.job->desc(r.chunk);
-        if ((e = cudaMemsetAsync(r.job->d_keys, 0, r.job->keys_bytes_per_dm() * d.n_dm, s)) != cudaSuccess)
-          return cuda_fail(e, "memset peaks");
-      }
+      // every valid segment's key is stored once by the search: no clearing
+      for (auto& r : kv.second) all.push_back(r);
     }
     for (auto& kv : classes) {
       const vk::SearchVariant v = p->variant[kv.first];
@@ -259,9 +255,8 @@ int autotune(volks_plan* p, std::pair<int, int> cls, const std::vector<RangeRef>
       cudaEventElapsedTime(&ms, a, b);
       if (rep > 0) ms_best = std::min(ms_best, ms);
     }
-    // a unit of a fold-f split covers 1/f of the band: cost of the whole
-    // band per (baseline, DM, tile, delay residue) = time per unit x f
-    const double per_point = ms_best / (double)units * vs[i].fold;
+    // a unit covers a whole tile (all delay residues) in every split
+    const double per_point = ms_best / (double)units;
     if (per_point < best) {
       best = per_point;
       best_v = vs[i];
