@@ -618,14 +618,6 @@ int volks_search_peaks_noalloc(const volks_segment *seg, const volks_params *prm
 int volks_noalloc_tables(void *cuda_stream, int32_t *shifts, int32_t *nvalid, int32_t n_dm,
                          int32_t n_f);
 
-/*
- * Measured FP32 FMA throughput of the current device in TFLOP/s (2 flops
- * per FMA): every SM runs 8 independent FMA chains per thread; timed with
- * CUDA events on cuda_stream after one warm-up launch (~1 ms each).  The
- * denominator of the FP32 search kernel's roofline, as a measurement.
- */
-int volks_measure_fp32_peak(void *cuda_stream, double *tflops);
-
 #ifdef __cplusplus
 }
 #endif

@@ -1,13 +1,19 @@
+// Benchmark helper, built into its own library (libvolks_bench.so) and
+// loaded by the benchmark only; not part of the search library's C ABI.
+//
 // FP32 FMA throughput of the device: the denominator of the FP32 search
 // kernel's roofline, measured rather than derived from the lane count and
 // clock.  Every thread runs 8 independent FMA chains (enough to cover the
 // FMA latency with 16 warps per SM); one launch covers every SM.
+//
+//   int bench_fp32_fma_tflops(void *cuda_stream, double *tflops);
+//
+// times two launches (the first warms up) with CUDA events on cuda_stream
+// and returns 0, or a CUDA error code (nonzero) on failure.
 #include <cstdint>
 
 #include <cuda_runtime.h>
 
-#include "../../include/volks.h"
-#include "volks_job.h"
 
 namespace vk {
 namespace {
@@ -35,20 +41,18 @@ __global__ void __launch_bounds__(kProbeThreads) fma_probe_kernel(float* out, in
 }  // namespace
 }  // namespace vk
 
-extern "C" int volks_measure_fp32_peak(void* cuda_stream, double* tflops) {
-  using vk::cuda_fail;
-  using vk::fail;
-  if (!tflops) return fail(VOLKS_EINVAL, "NULL output");
+extern "C" int bench_fp32_fma_tflops(void* cuda_stream, double* tflops) {
+  if (!tflops) return (int)cudaErrorInvalidValue;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   int dev = 0, n_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-  if (e != cudaSuccess) return cuda_fail(e, "device query");
+  if (e != cudaSuccess) return (int)e;
   const int blocks = 2 * n_sm, iters = 4096;
   float* d_out = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if ((e = cudaMallocAsync(reinterpret_cast<void**>(&d_out), blocks * sizeof(float), st)) != cudaSuccess)
-    return cuda_fail(e, "alloc");
+    return (int)e;
   e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   float ms = 0.f;
@@ -66,7 +70,7 @@ extern "C" int volks_measure_fp32_peak(void* cuda_stream, double* tflops) {
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return cuda_fail(e, "FP32 peak probe");
+  if (e != cudaSuccess) return (int)e;
   const double flops = 2.0 * 8 * vk::kProbeUnroll * (double)iters * vk::kProbeThreads * blocks;
   *tflops = ms > 0.f ? flops / (ms * 1e-3) / 1e12 : 0.0;
   return 0;

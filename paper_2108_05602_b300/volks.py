@@ -184,8 +184,6 @@ def lib() -> C.CDLL:
     L.volks_search_batch.restype = C.c_int
     L.volks_refit_pulses.argtypes = [P, C.POINTER(volks_candidate), I32, I32, C.POINTER(volks_refit)]
     L.volks_refit_pulses.restype = C.c_int
-    L.volks_measure_fp32_peak.argtypes = [P, C.POINTER(C.c_double)]
-    L.volks_measure_fp32_peak.restype = C.c_int
     L.volks_loc_default_params.argtypes = [C.POINTER(volks_loc_params)]
     L.volks_loc_default_params.restype = C.c_int
     L.volks_localize.argtypes = [C.POINTER(volks_loc_obs), I32, C.POINTER(volks_loc_params),
@@ -322,13 +320,6 @@ def volks_localize(tau_s, tau_cal_s, dtau_dalpha, dtau_ddelta, snr, proj_len_m,
     return dict(status=res.status, n_used=res.n_used, used=used[:n].astype(bool),
                 x=np.array(res.x[:]), cov=np.array(res.cov[:]).reshape(2, 2), rms_s=res.rms_s,
                 loo=loo[:n], outlier=res.outlier, x_clean=np.array(res.x_clean[:]))
-
-
-def volks_measure_fp32_peak(stream: int = 0) -> float:
-    """Measured FP32 FMA throughput of the device, TFLOP/s."""
-    t = C.c_double()
-    _check(lib().volks_measure_fp32_peak(C.c_void_p(stream), C.byref(t)), "volks_measure_fp32_peak")
-    return t.value
 
 
 def volks_cross_match(cands: Sequence[dict], min_baselines: int) -> List[dict]:
