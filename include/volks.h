@@ -318,26 +318,8 @@ int volks_result_stats(volks_result *res, int32_t bl, int32_t dm_idx,
  * factor with auto spectra) applied before dedispersion. */
 int volks_result_gains(volks_result *res, float *gains, size_t cap_floats);
 
-/*
- * Checking aid, outside the search: one 128-delay-cell block of the
- * tensor-core rate GEMM (Sec. 2.2 2-D search, Sec. 2.4.2 step 6 window
- * combine) of window `win` (2, 4, 8, 16 or 32 APs) at `precision` (VOLKS_BF16,
- * VOLKS_FP16 or VOLKS_FP8), through the same operand builders and MMA
- * issue as the search kernel, with operand scale 1.
- * y:   device complex64 [32][128] (APs x delay cells).
- * out: device float [128][256]; row c, column 8 win s + 2 q (+ 1) holds the
- *      real (imaginary) part of sum_{u < win} y[s win + u][c]
- *      exp(-2 pi i q u / (4 win)), q < 4 win, s < 32 / win, from y and the
- *      DFT coefficients rounded to the operand type, accumulated in FP32.
- * flags: VOLKS_CHECK_SKIP_MMA issues no MMA, so the kernel's bounded wait
- *      for the tensor cores (shortened to ~0.1 s here) runs out: the call
- *      must then return VOLKS_ETIMEOUT with the context still usable.
- * Synchronous (waits on the legacy default stream).  VOLKS_EINVAL for a
- * bad window, precision or flag, VOLKS_ETIMEOUT if the tensor cores did not
- * answer within the kernel's bounded wait, VOLKS_ECUDA otherwise.
- */
-#define VOLKS_CHECK_SKIP_MMA 1
-int volks_check_rate_gemm(const void *y, int32_t win, int32_t precision, int32_t flags, float *out);
+/* The checking entry points (tensor-core GEMM layout and fault path, the
+ * no-allocation variant's device tables) are declared in volks_check.h. */
 
 /* ---- batch plans --------------------------------------------------------
  *
@@ -604,19 +586,6 @@ int volks_localize(const volks_loc_obs *obs, int32_t n, const volks_loc_params *
 int volks_search_peaks_noalloc(const volks_segment *seg, const volks_params *prm,
                                void *cuda_stream, float *peak_power, int32_t *peak_cell);
 
-/*
- * Checking accessor of the no-allocation variant (no paper counterpart):
- * copies the shift table (int32 [n_dm][n_f]) and n_valid (int32 [n_dm])
- * that the last volks_search_peaks_noalloc call on the current device
- * computed on the GPU into caller device buffers, on cuda_stream (device
- * to device copies; nothing is allocated).  n_dm and n_f must be the last
- * call's; VOLKS_EINVAL if they are not, if no call has run on the device,
- * or if a buffer is not device memory of the current device.  The copies
- * read the shared scratch, so they race with a later call that overlaps
- * them on the GPU.
- */
-int volks_noalloc_tables(void *cuda_stream, int32_t *shifts, int32_t *nvalid, int32_t n_dm,
-                         int32_t n_f);
 
 #ifdef __cplusplus
 }

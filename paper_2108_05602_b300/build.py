@@ -26,7 +26,8 @@ SOURCES = ["volks_kernels.cu", "volks_mma.cu", "volks_api.cu", "volks_plan.cu", 
 BENCH_SOURCES = ["bench_probe.cu"]
 BENCH_LIB = os.path.join(HERE, "libvolks_bench.so")
 HEADERS = ["fft_regs.cuh", "twiddle_ce.h", "search_common.cuh", "search_kernel.cuh", "tcgen05.cuh", "volks_internal.h",
-           "volks_job.h", "volks_result.h", os.path.join("..", "..", "include", "volks.h")]
+           "volks_job.h", "volks_result.h", os.path.join("..", "..", "include", "volks.h"),
+           os.path.join("..", "..", "include", "volks_check.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

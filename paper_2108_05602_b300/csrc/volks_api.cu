@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/volks.h"
+#include "../../include/volks_check.h"
 #include "volks_internal.h"
 #include "volks_job.h"
 #include "volks_result.h"

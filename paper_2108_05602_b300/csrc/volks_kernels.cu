@@ -1,11 +1,12 @@
 // sm_103a kernels of the cross-spectrum single-pulse search.
 //
-//   prep     a2-a3  FP64 per-channel power, gains, normalise + calibrate +
+//   prep     a2-a3  per-channel power (FP64 accumulation), gains, normalise + calibrate +
 //                   transpose the visibilities to channel-major [b][k][t]
 //   search   a4-a7  fused: dedispersed gather of a 32-AP tile, delay FFT
-//                   (pad 4, one residue class of delay cells per CTA), rate
-//                   FFTs of every window, |Z|^2 and arg-max, all on chip;
-//                   one 64-bit atomicMax per (segment, CTA) to global memory
+//                   (pad 4, one residue class of delay cells per pass, every
+//                   residue of the tile in one unit), rate FFTs of every
+//                   window, |Z|^2 and arg-max, all on chip; one key store
+//                   per segment to global memory
 //   select   a8     FP64 series mean / std, z-score threshold -> bitmaps
 //   match    a9     per (baseline, DM) sweep over selected segments of all
 //                   windows in start order: overlap groups -> candidates
@@ -23,41 +24,68 @@
 namespace vk {
 
 // ============================================================== prep ====
-// Partial sums in FP64 over a chunk of APs, one thread per (frequency
-// point, AP phase); coalesced along frequency.  Row r of the grid's z axis
-// is (polarisation, baseline) summing |S|^2 of the cross spectrum, or, with
-// auto spectra, (polarisation, station) summing a^2.
-template <bool AUTO>
+// Partial sums over a chunk of APs.  Row r of the grid's z axis is
+// (polarisation, baseline) summing |S|^2 of the cross spectrum, or, with
+// auto spectra, (polarisation, station) summing a^2.  Each thread owns two
+// adjacent frequency points (one 16-byte load of two complex values, or 8
+// bytes of two auto powers) and one AP phase of 8; four APs are loaded at
+// once, their squares summed in FP32 (a few terms, one rounding each) and
+// that sum accumulated in FP64 over the chunk, so the per-point power over
+// the segment is an FP64 accumulation.  VEC = false takes the same path
+// with 8-byte loads when the caller's buffer is not 16-byte aligned.
+template <bool AUTO, bool VEC>
 __global__ void __launch_bounds__(256) chan_power_kernel(const PrepArgs a) {
-  __shared__ double red[8][33];
-  const int k = blockIdx.x * 32 + threadIdx.x;
+  __shared__ double red[8][2][33];
+  const int k = 2 * (blockIdx.x * 32 + threadIdx.x);
   const int tc = blockIdx.y, row = blockIdx.z;
   const int t_beg = tc * a.tchunk;
   const int t_end = min(a.n_ap, t_beg + a.tchunk);
-  double s = 0.0;
-  if (k < a.n_f) {
-    if (AUTO) {
-      const float* v = a.autos + (size_t)row * a.n_ap * a.n_f + k;
-      for (int t = t_beg + (int)threadIdx.y; t < t_end; t += 8) {
-        const double x = (double)v[(size_t)t * a.n_f];
-        s = fma(x, x, s);
+  double s0 = 0.0, s1 = 0.0;
+  if (k < a.n_f) {  // n_f is even
+    // (power of point k, power of point k + 1) of AP t
+    auto pw = [&](int t) -> float2 {
+      if constexpr (AUTO) {
+        const float* v = a.autos + ((size_t)row * a.n_ap + t) * a.n_f + k;
+        float2 x;
+        if constexpr (VEC) {
+          x = __ldg(reinterpret_cast<const float2*>(v));
+        } else {
+          x = make_float2(__ldg(v), __ldg(v + 1));
+        }
+        return make_float2(x.x * x.x, x.y * x.y);
+      } else {
+        const float2* v = a.vis + ((size_t)row * a.n_ap + t) * a.n_f + k;
+        float4 x;
+        if constexpr (VEC) {
+          x = __ldg(reinterpret_cast<const float4*>(v));
+        } else {
+          const float2 u = __ldg(v), w = __ldg(v + 1);
+          x = make_float4(u.x, u.y, w.x, w.y);
+        }
+        return make_float2(fmaf(x.y, x.y, x.x * x.x), fmaf(x.w, x.w, x.z * x.z));
       }
-    } else {
-      const float2* v = a.vis + (size_t)row * a.n_ap * a.n_f + k;
-      for (int t = t_beg + (int)threadIdx.y; t < t_end; t += 8) {
-        const float2 x = v[(size_t)t * a.n_f];
-        s = fma((double)x.x, (double)x.x, s);
-        s = fma((double)x.y, (double)x.y, s);
-      }
+    };
+    int t = t_beg + (int)threadIdx.y;
+    for (; t + 24 < t_end; t += 32) {
+      const float2 p0 = pw(t), p1 = pw(t + 8), p2 = pw(t + 16), p3 = pw(t + 24);
+      s0 += (double)((p0.x + p1.x) + (p2.x + p3.x));
+      s1 += (double)((p0.y + p1.y) + (p2.y + p3.y));
+    }
+    for (; t < t_end; t += 8) {
+      const float2 p0 = pw(t);
+      s0 += (double)p0.x;
+      s1 += (double)p0.y;
     }
   }
-  red[threadIdx.y][threadIdx.x] = s;
+  red[threadIdx.y][0][threadIdx.x] = s0;
+  red[threadIdx.y][1][threadIdx.x] = s1;
   __syncthreads();
-  if (threadIdx.y == 0 && k < a.n_f) {
-    double t = 0.0;
+  if (threadIdx.y < 2 && k < a.n_f) {
+    const int j = threadIdx.y;
+    double v = 0.0;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) t += red[i][threadIdx.x];
-    a.part[((size_t)row * a.n_tchunk + tc) * a.n_f + k] = t;
+    for (int i = 0; i < 8; ++i) v += red[i][j][threadIdx.x];
+    a.part[((size_t)row * a.n_tchunk + tc) * a.n_f + k + j] = v;
   }
 }
 
@@ -137,10 +165,20 @@ cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s, int* n_launch) {
   const bool autos = a.normalize && a.autos;
   const int rows = a.n_pol * (autos ? a.n_st : a.n_bl);
   if (a.normalize) {
-    if (autos)
-      chan_power_kernel<true><<<dim3((a.n_f + 31) / 32, a.n_tchunk, rows), blk, 0, s>>>(a);
-    else
-      chan_power_kernel<false><<<dim3((a.n_f + 31) / 32, a.n_tchunk, rows), blk, 0, s>>>(a);
+    // two frequency points per thread: bands have an even number of points
+    if (a.n_f & 1) return cudaErrorInvalidValue;
+    const dim3 g((a.n_f + 63) / 64, a.n_tchunk, rows);
+    if (autos) {
+      if ((reinterpret_cast<uintptr_t>(a.autos) & 7) == 0)
+        chan_power_kernel<true, true><<<g, blk, 0, s>>>(a);
+      else
+        chan_power_kernel<true, false><<<g, blk, 0, s>>>(a);
+    } else {
+      if ((reinterpret_cast<uintptr_t>(a.vis) & 15) == 0)
+        chan_power_kernel<false, true><<<g, blk, 0, s>>>(a);
+      else
+        chan_power_kernel<false, false><<<g, blk, 0, s>>>(a);
+    }
     *n_launch += 1;
   }
   gain_kernel<<<(a.n_pol * a.n_bl * a.n_f + 255) / 256, 256, 0, s>>>(a);

@@ -32,6 +32,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/volks.h"
+#include "../../include/volks_check.h"
 #include "volks_internal.h"
 
 namespace {

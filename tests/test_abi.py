@@ -17,6 +17,7 @@ from paper_2108_05602_b300 import volks as V
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "volks.h")
+HEADERS = [HEADER, os.path.join(ROOT, "include", "volks_check.h")]
 
 
 @pytest.fixture(scope="module")
@@ -26,7 +27,7 @@ def L():
 
 
 def declared_functions():
-    src = open(HEADER).read()
+    src = "".join(open(h).read() for h in HEADERS)
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(volks_\w+)\s*\(", src)))
 
