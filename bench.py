@@ -82,6 +82,16 @@ def workload(name="evn_fp32"):
     return WORKLOADS[name](synth)
 
 
+def workload_config(name, wl, trials):
+    """The `config` object both arms report for a scan workload."""
+    return {"workload": name, "n_bl": wl.n_bl, "n_ap": wl.n_ap, "n_if": wl.n_if, "n_chan": wl.n_chan,
+            "n_dm": wl.n_dm, "dm": [wl.dm_lo, wl.dm_lo + wl.dm_step * (wl.n_dm - 1)],
+            "windows": list(wl.windows), "pad_delay": wl.pad_delay, "pad_rate": wl.pad_rate,
+            "trials_per_step": trials, "input_bytes": wl.n_bl * wl.n_ap * wl.n_f * 8,
+            "l2": "inputs larger than L2 (3.6 GB per step)" if wl.n_bl * wl.n_ap * wl.n_f * 8 > (126 << 20)
+            else "inputs smaller than L2"}
+
+
 def trial_count(wl, nvalid) -> int:
     n = 0
     for nv in nvalid:
@@ -485,11 +495,18 @@ def serving_summary(precisions=("fp32", "bf16"), rate_hz=20.0, duration_s=20.0, 
 
 
 def run_reference(args):
+    """The FP64 oracle, as it stands, on the host cores: each step is a
+    bounded sample of the EVN-scale workload (1 baseline x 8 DM trials x
+    5 s), the value is trials/s of that sample; the line carries the same
+    config as the GPU arm."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    from oracle import volks_oracle as O
     from paper_2108_05602_b300 import synth
     wl = workload()
+    sh = O.shift_table(wl.f_lo_mhz, wl.chan_bw_mhz, wl.n_f, wl.dms(), wl.t_ap_s)
+    trials_full = trial_count(wl, [O.n_valid(wl.n_ap, r) for r in sh])
     cores = min(8, os.cpu_count() or 1)
     n_ap = 4883  # 5 s of the scan
     dms = list(range(0, wl.n_dm, wl.n_dm // cores))[:cores]
@@ -505,11 +522,11 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "evn_sample", "n_bl": 1, "n_ap": n_ap, "n_dm": len(dms),
-                       "n_f": wl.n_f, "windows": list(wl.windows)},
+            "config": workload_config("evn_fp32", wl, trials_full),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"1 baseline x {len(dms)} DM trials x {n_ap} APs "
-                                       "(5 s) of the EVN-scale workload, FP64 numpy"},
+                             "sample": f"each step: 1 baseline x {len(dms)} DM trials x {n_ap} APs "
+                                       f"(5 s) of this workload, {n} trials, FP64 numpy, one spawned "
+                                       "process per DM trial"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -712,14 +729,8 @@ def run_volks(args):
             "ms_per_step": t_max_s * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[prec],
             "data": "synthetic: complex64 N(0,1) noise + 20 dispersed pulses + station RFI",
-            "config": {"workload": args.workload, "n_bl": wl.n_bl, "n_ap": wl.n_ap,
-                       "n_if": wl.n_if, "n_chan": wl.n_chan, "n_dm": wl.n_dm,
-                       "dm": [wl.dm_lo, wl.dm_lo + wl.dm_step * (wl.n_dm - 1)],
-                       "windows": list(wl.windows), "pad_delay": wl.pad_delay,
-                       "pad_rate": wl.pad_rate, "trials_per_step": trials,
-                       "input_bytes": wl.n_bl * wl.n_ap * wl.n_f * 8,
-                       "l2": "inputs larger than L2 (3.6 GB per step)",
-                       "step_ms_p50": srt[len(srt) // 2], "step_ms_p99": srt[-1]},
+            "config": dict(workload_config(args.workload, wl, trials),
+                           step_ms_p50=srt[len(srt) // 2], step_ms_p99=srt[-1]),
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "steps": e2e_steps,
