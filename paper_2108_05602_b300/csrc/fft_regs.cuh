@@ -36,26 +36,41 @@ constexpr int bitrev(int x, int bits) {
 }
 
 // ---- complex helpers -----------------------------------------------------
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+
 // Complex add and subtract as one packed FP32x2 instruction each (sm_100
-// family): the same IEEE round-to-nearest result per component as two
-// scalar operations, in half the issue slots.
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) {
-  unsigned long long ra, rb, rd;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
-  asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
-  float2 d;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(rd));
-  return d;
+// family) when PK: the same IEEE round-to-nearest result per component as
+// two scalar operations, in half the issue slots.  The FP32 search kernel
+// is issue-bound and takes the packed form; the tensor-core kernel, bound
+// by latency in its GEMM phase, measured ~2.5 % faster with the scalar one.
+template <bool PK>
+__device__ __forceinline__ float2 cadd_t(float2 a, float2 b) {
+  if constexpr (PK) {
+    unsigned long long ra, rb, rd;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+    float2 d;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(rd));
+    return d;
+  } else {
+    return cadd(a, b);
+  }
 }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) {
-  unsigned long long ra, rb, rd;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
-  asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
-  float2 d;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(rd));
-  return d;
+template <bool PK>
+__device__ __forceinline__ float2 csub_t(float2 a, float2 b) {
+  if constexpr (PK) {
+    unsigned long long ra, rb, rd;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+    float2 d;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(rd));
+    return d;
+  } else {
+    return csub(a, b);
+  }
 }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
@@ -94,7 +109,7 @@ __device__ __forceinline__ float2 twiddle(float2 v) {
 
 // In-place radix-2 decimation-in-frequency FFT of N points held in
 // registers: natural-order input, output X[k] left at position bitrev(k).
-template <int N>
+template <int N, bool PK = true>
 __device__ __forceinline__ void fft_dif(float2 (&x)[N]) {
   constexpr int L = ilog2(N);
   static_for<0, L>([&](auto st) {
@@ -104,8 +119,8 @@ __device__ __forceinline__ void fft_dif(float2 (&x)[N]) {
         constexpr int i0 = decltype(blk)::value * 2 * half + decltype(j)::value;
         constexpr int i1 = i0 + half;
         const float2 a = x[i0], b = x[i1];
-        x[i0] = cadd(a, b);
-        x[i1] = twiddle<2 * half, decltype(j)::value>(csub(a, b));
+        x[i0] = cadd_t<PK>(a, b);
+        x[i1] = twiddle<2 * half, decltype(j)::value>(csub_t<PK>(a, b));
       });
     });
   });
@@ -138,9 +153,9 @@ __device__ __forceinline__ void fft3_nat(float2 (&x)[N]) {
     const float2 a = f[0][P];
     const float2 b = twiddle<N, K2>(f[1][P]);
     const float2 c = twiddle<N, 2 * K2>(f[2][P]);
-    const float2 sum = cadd(b, c), dif = csub(b, c);
+    const float2 sum = cadd_t<true>(b, c), dif = csub_t<true>(b, c);
     const float2 t = make_float2(fmaf(-0.5f, sum.x, a.x), fmaf(-0.5f, sum.y, a.y));
-    x[K2] = cadd(a, sum);
+    x[K2] = cadd_t<true>(a, sum);
     x[K2 + Q] = make_float2(fmaf(h, dif.y, t.x), fmaf(-h, dif.x, t.y));      // t - i h dif
     x[K2 + 2 * Q] = make_float2(fmaf(-h, dif.y, t.x), fmaf(h, dif.x, t.y));  // t + i h dif
   });

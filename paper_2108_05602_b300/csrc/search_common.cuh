@@ -70,7 +70,7 @@ __device__ __forceinline__ void rate_window(const float2* __restrict__ S, int c,
     uint32_t bq;
     if constexpr (R == 1) {
       float2 z = col[0];
-      static_for<1, W>([&](auto u) { z = cadd(z, col[decltype(u)::value * LD]); });
+      static_for<1, W>([&](auto u) { z = cadd_t<true>(z, col[decltype(u)::value * LD]); });
       best = cabs2(z);
       bq = 0;
     } else if constexpr (W == 2 && R == 8) {
@@ -182,7 +182,7 @@ __device__ __forceinline__ void store_keys(const UnitState& us, const unsigned l
 // in S; the rate stage (FP32 register FFTs or the tensor-core GEMM) follows.
 // Called by every thread of the CTA after `us` has been filled and
 // synchronised; returns after a barrier, with Y complete in S.
-template <int N1, int FOLD>
+template <int N1, int FOLD, bool PK = true>
 __device__ __forceinline__ void delay_stage(const UnitState& us, float2* S) {
   constexpr int N = 32 * N1;
   // N1 a power of two (radix-2 register FFTs, each warp owns 32 / N1
@@ -224,14 +224,14 @@ __device__ __forceinline__ void delay_stage(const UnitState& us, float2* S) {
           if constexpr (F == 0) {
             v = u;
           } else {
-            v = cadd(v, cmul(u, wf[F]));
+            v = cadd_t<PK>(v, cmul(u, wf[F]));
           }
         });
         if (r != 0) v = cmul(v, __ldg(tw_m + k * r));  // k < N, r < P: k r < M
         x[K1] = v;
       });
       if constexpr (kPow2) {
-        fft_dif<N1>(x);
+        fft_dif<N1, PK>(x);
       } else {
         fft3_nat<N1>(x);
       }
@@ -252,7 +252,7 @@ __device__ __forceinline__ void delay_stage(const UnitState& us, float2* S) {
       constexpr int K0 = decltype(kk0)::value;
       y[K0] = S[lane * LD + K0 * N1 + warp];
     });
-    fft_dif<32>(y);
+    fft_dif<32, PK>(y);
     __syncthreads();
     static_for<0, 32>([&](auto mm2) {
       constexpr int M2 = decltype(mm2)::value;

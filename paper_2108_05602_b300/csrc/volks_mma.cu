@@ -293,7 +293,7 @@ __device__ __forceinline__ void refine_column(const float2* __restrict__ S, int 
     const float2 v = S[(u0 + U) * LD + c];
     y[U] = U == 0 ? v : cmul(v, __ldg(tw_m + U * rho * step));
   });
-  fft_dif<W>(y);
+  fft_dif<W, false>(y);
   uint32_t vq;
   argmax_tree<0, W>([&](auto qq) { return cabs2(y[bitrev(decltype(qq)::value, ilog2(W))]); }, best, vq);
   bq = 4u * vq + (uint32_t)rho;
@@ -541,7 +541,7 @@ __device__ __forceinline__ bool mma_tile(const UnitState& us, uint8_t* smem, Mma
   unsigned long long* best = reinterpret_cast<unsigned long long*>(smem + L::OFF_BEST);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-  delay_stage<N1, FOLD>(us, S);
+  delay_stage<N1, FOLD, false>(us, S);
 
   const int win_mask = us.a.win_mask;
   const int t0 = us.t0, nv = us.nv, r = us.r;
