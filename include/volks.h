@@ -38,18 +38,19 @@ extern "C" {
  * VOLKS_FP32: every delay and rate cell is evaluated in FP32 on the CUDA
  * cores (register FFTs).
  * VOLKS_BF16, VOLKS_FP16, VOLKS_FP8: the delay transform stays FP32; the
- * fringe-rate transform of the 2..32-AP windows of a 2-D search
+ * fringe-rate transform of the 4..32-AP windows of a 2-D search
  * (pad_rate 4, Sec. 2.2) is a coarse DFT-matrix GEMM on the tensor cores
  * with operands in BF16, FP16 or FP8 E4M3 (a power-of-two scale per 32-AP
  * tile for FP16 and FP8) and FP32 accumulation.  Per segment and delay
  * residue class, the delay cells whose coarse power is within a margin of
- * the coarse maximum (1/16 for BF16, 1/64 for FP16; any for FP8), at most
- * the 8 largest, are then re-evaluated in FP32 over all their rate cells,
- * and the peak is the largest FP32 value among them; 1-AP windows are
- * always FP32.  A peak therefore differs from the FP32 search only when
- * the FP32 peak's delay cell is not among those retained, which needs a
- * near-tie at the coarse precision.  1-D searches
- * (pad_rate 0) and bands under 256 points run FP32 whatever is asked.
+ * the coarse maximum (1/16 for BF16, 1/64 for FP16, 1/4 for FP8; halved
+ * while more than 8 pass), at most 8, are then re-evaluated in FP32 over
+ * all their rate cells, and the peak is the largest FP32 value among
+ * them; 1- and 2-AP windows are always FP32.  A peak therefore differs
+ * from the FP32 search only when the FP32 peak's delay cell is not among
+ * those retained, which needs a near-tie at the coarse precision.  1-D
+ * searches (pad_rate 0) and bands under 256 points run FP32 whatever is
+ * asked.
  */
 #define VOLKS_FP32 0
 #define VOLKS_BF16 1
@@ -324,8 +325,8 @@ int volks_result_gains(volks_result *res, float *gains, size_t cap_floats);
 /* ---- batch plans --------------------------------------------------------
  *
  * A plan searches many segments of different shapes (baselines, APs, IFs,
- * channels, DM grids, windows) together: the per-(baseline, DM, tile,
- * residue) work of all segments of one band class (n_f, pad_rate) is done
+ * channels, DM grids, windows) together: the per-(baseline, DM, tile)
+ * work of all segments of one band class (n_f, pad_rate) is done
  * by one persistent search launch whose CTAs pull work from a shared
  * counter, followed by one select and one match launch over all segments.
  * Results are those of volks_search_segment on each segment.

@@ -16,9 +16,9 @@
 namespace vk {
 
 // ============================================================ search ====
-// Stage 3 of one unit on CUDA cores after the delay stage: thread = delay
-// column c, FP32 rate FFTs of every window, |Z|^2 and arg-max, merged over
-// the warps and published as one 64-bit atomicMax per segment.
+// Stage 3 of one residue pass on CUDA cores after the delay stage: thread =
+// delay column c, FP32 rate FFTs of every window, |Z|^2 and arg-max, merged
+// over the warps into the tile's running key of each segment.
 // Windows searched by a sliding-form unit whose tile starts at AP t0 (phase
 // phi = t0 mod 32): those wider than phi.
 __device__ __forceinline__ int sliding_windows(int win_mask, int t0) {

@@ -4,31 +4,34 @@
 // in tensor memory), followed by an FP32 re-evaluation of the best delay
 // columns of every segment.
 //
-// Per work unit (baseline, DM trial, 32-AP tile, delay residue r):
+// Per work unit (baseline, DM trial, 32-AP tile), for each delay residue r
+// in turn:
 //   delay   stages 0-2 of the FP32 kernel (shared code): FP32 delay
 //           spectrum Y[t][c] of the tile's 32 APs x N = 32 N1 delay cells
 //           in shared memory S.
-//   w=1,2   exact FP32 windows on the CUDA cores, one warp per segment,
-//           while the first GEMMs run.
 //   GEMM    per M-block of 128 delay cells: A = Y^T rounded to the operand
 //           type (rows = delay cells, K = 32 APs x (re, im)); per window w,
 //           B = the real embedding of the R = 4w point rate DFT of each
 //           segment, so D[c][2q + {0,1}] = (Re, Im) Z_w[s, q, c]
-//           (Sec. 2.2 2-D search; Sec. 2.4.2 step 6 window combine).  Warp
-//           0 issues the MMAs; two 256-column TMEM buffers let the other
-//           warps drain one (M-block, window) job while the next one runs.
-//   coarse  epilogue: per (segment, delay cell) the largest coarse |Z|^2
-//           over the segment's rate cells; a warp per segment keeps the
-//           8 delay cells with the largest coarse values (ties: lower cell).
-//   refine  the 8 retained delay cells of every segment are re-evaluated in
+//           (Sec. 2.2 2-D search; Sec. 2.4.2 step 6 window combine).  One
+//           thread issues the MMAs; two 256-column TMEM buffers let a
+//           warpgroup drain one (M-block, window) job while the next runs.
+//   coarse  the drain warps store per (segment, delay cell) the largest
+//           coarse |Z|^2 over the segment's rate cells; helper warps merge
+//           each block's cells within delta of the segment's running
+//           maximum into a candidate list (at most 8 are kept).
+//   w=1,2   exact FP32 windows on the CUDA cores, taken in pieces by the
+//           helper warps while they wait.
+//   refine  the retained delay cells of every segment are re-evaluated in
 //           FP32 from S (all R rate cells of each: pre-twiddled w-point
 //           register FFTs, as the FP32 kernel computes them); the segment's
 //           peak is the largest refined power, ties to the lowest q M + m.
-//   publish one 64-bit atomicMax per segment, as the FP32 kernel.
+//   publish the residue's keys fold into the tile's running keys; each
+//           key is stored once after the tile's last residue.
 //
 // Reported peaks are therefore FP32 evaluations of real grid cells; they
-// equal the FP32 search whenever its peak cell lies in one of the 8 delay
-// cells the coarse pass ranks highest for that segment.
+// equal the FP32 search whenever its peak cell lies in one of the delay
+// cells the coarse pass retains for that segment.
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
@@ -217,54 +220,6 @@ __device__ __forceinline__ void issue_window_t(uint64_t ad, uint64_t bd, uint32_
   }
 }
 
-// One MMA of a window's job: K byte offset into the A block, byte offset
-// into the window's B (both multiples of 16), TMEM column, and the
-// instruction descriptor with the accumulate flag in bit 31.
-struct MmaOp {
-  uint16_t a16, b16, dcol;
-  uint16_t _pad;
-  uint32_t idesc_acc;
-};
-constexpr int kMaxOpsPerJob = 4;
-
-// The MMAs of window 2^l (same sequence as issue_window_t) into ops[].
-template <int PREC>
-__device__ int job_ops(int l, MmaOp* ops) {
-  using O = Op<PREC>;
-  constexpr int EB = O::EB;
-  const int w = 1 << l;
-  const int seg_kb = 2 * w * EB;
-  int n_ops = 0;
-  if (seg_kb >= 32) {
-    const int nseg = 32 / w, n = 8 * w, ks = seg_kb / 32;
-    const uint32_t idesc = PREC == VOLKS_FP8 ? tc::idesc_e4m3(n) : tc::idesc_f16(n, PREC == VOLKS_BF16);
-    for (int s = 0; s < nseg; ++s)
-      for (int k = 0; k < ks; ++k)
-        ops[n_ops++] = MmaOp{(uint16_t)((seg_kb * s + 32 * k) >> 4), (uint16_t)((32 * k) >> 4),
-                             (uint16_t)(n * s), 0, idesc | (k > 0 ? 0x80000000u : 0u)};
-  } else {
-    const int g = 32 / seg_kb, n = 8 * w * g, ngrp = (32 / w) / g;
-    const uint32_t idesc = PREC == VOLKS_FP8 ? tc::idesc_e4m3(n) : tc::idesc_f16(n, PREC == VOLKS_BF16);
-    for (int p = 0; p < ngrp; ++p)
-      ops[n_ops++] = MmaOp{(uint16_t)((32 * p) >> 4), 0, (uint16_t)(n * p), 0, idesc};
-  }
-  return n_ops;
-}
-
-// Issue one job from its op table: a compact loop, so the issuing warp's
-// code stays small and resident in the instruction cache.
-template <int PREC>
-__device__ __forceinline__ void issue_ops(const MmaOp* ops, int n_ops, uint64_t ad, uint64_t bd, uint32_t d) {
-#pragma unroll 1
-  for (int i = 0; i < n_ops; ++i) {
-    const MmaOp o = ops[i];
-    const uint32_t idesc = o.idesc_acc & 0x7fffffffu;
-    const bool acc = (o.idesc_acc >> 31) != 0;
-    if constexpr (PREC == VOLKS_FP8) tc::mma_f8(d + o.dcol, ad + o.a16, bd + o.b16, idesc, acc);
-    else tc::mma_f16(d + o.dcol, ad + o.a16, bd + o.b16, idesc, acc);
-  }
-}
-
 template <int PREC>
 __device__ __forceinline__ void issue_window(int l, uint32_t a_base, uint32_t b_base, uint32_t d) {
   using O = Op<PREC>;
@@ -322,10 +277,9 @@ struct MmaCtx {
 constexpr int PB_FULL = 0, PB_AFULL = 2, PB_CFREE = 4, PB_ADONE = 6, PB_CDONE = 8;
 __device__ __forceinline__ uint32_t pbit(uint32_t par, int b) { return (par >> b) & 1u; }
 
+// Operand descriptors, built once per CTA.
 struct JobTable {
-  MmaOp ops[6][kMaxOpsPerJob];  // by window log2 (1..5)
-  int n_ops[6];
-  uint64_t bd[6];               // B descriptor of each window
+  uint64_t bd[6];               // B descriptor of each GEMM window (log2 2..5)
   uint64_t ad[2];               // A descriptor of each A buffer
 };
 
@@ -843,10 +797,8 @@ __global__ void __launch_bounds__(32 * N1, 1) search_mma_kernel(const __grid_con
   build_rate_dft<PREC, 2>(smem + L::OFF_B, p.d[0].tw_m, p.d[0].M, tid, N);
   if (tid == 0) {
     constexpr int NWG = N1 >= 16 ? 2 : 1, NHELP = N1 - 1 - 4 * NWG;
-    for (int l = 1; l <= 5; ++l) {
-      jt.n_ops[l] = job_ops<PREC>(l, jt.ops[l]);
-      if (l >= 2)
-        jt.bd[l] = tc::sdesc_sw(tc::smem_u32(smem + L::OFF_B + Op<PREC>::b_off(l) - Op<PREC>::b_off(2)),
+    for (int l = 2; l <= 5; ++l) {
+      jt.bd[l] = tc::sdesc_sw(tc::smem_u32(smem + L::OFF_B + Op<PREC>::b_off(l) - Op<PREC>::b_off(2)),
                               (uint32_t)Op<PREC>::b_row_bytes(l));
     }
     for (int i = 0; i < 2; ++i) {
