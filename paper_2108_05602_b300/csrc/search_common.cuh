@@ -109,6 +109,54 @@ __device__ __forceinline__ void rate_window(const float2* __restrict__ S, int c,
   }
 }
 
+// The 2-AP window of the 2-D search (R = 8) with one warp per segment:
+// each lane walks N1 delay columns (c = lane + 32 j) keeping the column with
+// the largest cell, whose power is r0 + max(|2 rx|, |2 ry|, |sqrt2 (rx +
+// ry)|, |sqrt2 (ry - rx)|) -- the same FP32 expressions as rate_cells_w2, so
+// by monotonic rounding it equals the largest of the column's eight cells --
+// and resolves that column's rate cell once (lowest q on ties; equal powers
+// in one lane keep the lower column).  The warp's best goes to the
+// segment's first slot, the other N1 - 1 slots get an entry that never wins.
+template <int N1, bool SLIDE>
+__device__ __forceinline__ void rate_window_w2_seg(const float2* __restrict__ S, uint32_t M, int Pd, int r,
+                                                   int t0, int nv, int slot0, uint2* slot, int warp, int lane) {
+  constexpr int N = 32 * N1, LD = N + 1, W = 2, NSEG = kTile / W;
+  const int nseg = SLIDE ? min(NSEG, max(0, nv - t0) / W) : min(NSEG, max(0, nv / W - t0 / W));
+#pragma unroll 1
+  for (int s = warp; s < nseg; s += N1) {
+    const float2* y0p = S + (2 * s) * LD;
+    const float2* y1p = y0p + LD;
+    float bp = -1.f;
+    int bc = lane;
+#pragma unroll 4
+    for (int jj = 0; jj < N1; ++jj) {
+      const int c = lane + 32 * jj;
+      const float2 y0 = y0p[c], y1 = y1p[c];
+      const float r0 = fmaf(y1.y, y1.y, fmaf(y1.x, y1.x, cabs2(y0)));
+      const float rx = fmaf(y1.y, y0.y, y1.x * y0.x);
+      const float ry = fmaf(y1.y, y0.x, -(y1.x * y0.y));
+      constexpr float kS2 = Tw<8, 1>::re * 2.0f;
+      const float a = rx + rx, bb = ry + ry;
+      const float cc = kS2 * (rx + ry), dd = kS2 * (ry - rx);
+      const float pm = r0 + fmaxf(fmaxf(fabsf(a), fabsf(bb)), fmaxf(fabsf(cc), fabsf(dd)));
+      if (pm > bp) {
+        bp = pm;
+        bc = c;
+      }
+    }
+    float P8[8];
+    rate_cells_w2(y0p[bc], y1p[bc], P8);
+    float pv;
+    uint32_t qv;
+    argmax_tree<0, 8>([&](auto qq) { return P8[decltype(qq)::value]; }, pv, qv);
+    const uint32_t lin = qv * M + (uint32_t)(bc * Pd + r);
+    const uint32_t pb = __float_as_uint(pv);
+    const uint32_t wmax = __reduce_max_sync(0xffffffffu, pb);
+    const uint32_t wlin = __reduce_min_sync(0xffffffffu, pb == wmax ? lin : 0xffffffffu);
+    if (lane < N1) slot[(slot0 + s) * N1 + lane] = lane == 0 ? make_uint2(wmax, wlin) : make_uint2(0u, 0xffffffffu);
+  }
+}
+
 // Range holding work unit u (ranges are in increasing `base` order).
 __device__ __forceinline__ int find_desc(const Batch& p, long long u) {
   int lo = 0, hi = p.n_desc - 1;

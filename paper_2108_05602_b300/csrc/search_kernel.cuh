@@ -49,7 +49,12 @@ __device__ __forceinline__ void search_tile(const UnitState& us, float2* S, uint
     const uint32_t M = (uint32_t)us.a.M;
     const int t0 = us.t0, nv = us.nv;
     if (win_mask & 1) rate_window<1, PADR, N1, SLIDE>(S, c, m, M, t0, nv, slot_base(0), slot, warp, lane);
-    if (win_mask & 2) rate_window<2, PADR, N1, SLIDE>(S, c, m, M, t0, nv, slot_base(1), slot, warp, lane);
+    if (win_mask & 2) {
+      if constexpr (PADR == 4)
+        rate_window_w2_seg<N1, SLIDE>(S, M, P, us.r, t0, nv, slot_base(1), slot, warp, lane);
+      else
+        rate_window<2, PADR, N1, SLIDE>(S, c, m, M, t0, nv, slot_base(1), slot, warp, lane);
+    }
     if (win_mask & 4) rate_window<4, PADR, N1, SLIDE>(S, c, m, M, t0, nv, slot_base(2), slot, warp, lane);
     if (win_mask & 8) rate_window<8, PADR, N1, SLIDE>(S, c, m, M, t0, nv, slot_base(3), slot, warp, lane);
     if (win_mask & 16) rate_window<16, PADR, N1, SLIDE>(S, c, m, M, t0, nv, slot_base(4), slot, warp, lane);
