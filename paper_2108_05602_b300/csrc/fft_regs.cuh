@@ -42,8 +42,9 @@ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(
 // Complex add and subtract as one packed FP32x2 instruction each (sm_100
 // family) when PK: the same IEEE round-to-nearest result per component as
 // two scalar operations, in half the issue slots.  The FP32 search kernel
-// is issue-bound and takes the packed form; the tensor-core kernel, bound
-// by latency in its GEMM phase, measured ~2.5 % faster with the scalar one.
+// is issue-bound and takes the packed form throughout; the tensor-core
+// kernel measured faster with scalar adds in its delay stage (either half
+// packed was 2-5 % slower) and with packed adds in its re-evaluation FFTs.
 template <bool PK>
 __device__ __forceinline__ float2 cadd_t(float2 a, float2 b) {
   if constexpr (PK) {

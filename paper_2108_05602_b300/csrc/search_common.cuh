@@ -230,7 +230,7 @@ __device__ __forceinline__ void store_keys(const UnitState& us, const unsigned l
 // in S; the rate stage (FP32 register FFTs or the tensor-core GEMM) follows.
 // Called by every thread of the CTA after `us` has been filled and
 // synchronised; returns after a barrier, with Y complete in S.
-template <int N1, int FOLD, bool PK = true>
+template <int N1, int FOLD, bool PK = true, bool PK2 = PK>
 __device__ __forceinline__ void delay_stage(const UnitState& us, float2* S) {
   constexpr int N = 32 * N1;
   // N1 a power of two (radix-2 register FFTs, each warp owns 32 / N1
@@ -300,7 +300,7 @@ __device__ __forceinline__ void delay_stage(const UnitState& us, float2* S) {
       constexpr int K0 = decltype(kk0)::value;
       y[K0] = S[lane * LD + K0 * N1 + warp];
     });
-    fft_dif<32, PK>(y);
+    fft_dif<32, PK2>(y);
     __syncthreads();
     static_for<0, 32>([&](auto mm2) {
       constexpr int M2 = decltype(mm2)::value;

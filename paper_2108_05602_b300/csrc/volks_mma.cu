@@ -248,7 +248,7 @@ __device__ __forceinline__ void refine_column(const float2* __restrict__ S, int 
     const float2 v = S[(u0 + U) * LD + c];
     y[U] = U == 0 ? v : cmul(v, __ldg(tw_m + U * rho * step));
   });
-  fft_dif<W, false>(y);
+  fft_dif<W, true>(y);
   uint32_t vq;
   argmax_tree<0, W>([&](auto qq) { return cabs2(y[bitrev(decltype(qq)::value, ilog2(W))]); }, best, vq);
   bq = 4u * vq + (uint32_t)rho;
