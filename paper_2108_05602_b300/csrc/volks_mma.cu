@@ -475,7 +475,9 @@ __device__ __forceinline__ int finish_list(uint2* lst, const int* lcount, const 
 //   helper warps     the others: the exact 1- and 2-AP windows, the A blocks
 //                    from the third on (once `adone` says the MMAs reading the
 //                    buffer are complete), and the candidate merges of each
-//                    block (once every drain warp passed `cdone`).
+//                    block but the last (once every drain warp passed
+//                    `cdone`); after the phase every warp merges the last
+//                    block of the segment it then refines.
 template <int N1, int FOLD, int PREC>
 __device__ __forceinline__ bool mma_tile(const UnitState& us, uint8_t* smem, MmaCtx& cx, MmaBars& bars,
                                          const JobTable& jt, float* s_amax, unsigned int* err,
@@ -721,6 +723,13 @@ __device__ __forceinline__ bool mma_tile(const UnitState& us, uint8_t* smem, Mma
           __syncwarp();
           if (lane == 0) mbar_arrive(&bars.afull[b & 1]);
         }
+        if (b == NMB - 1) {
+          // the last block is merged after the GEMM phase by every warp (one
+          // segment each, fused with its refinement); the drain warps have
+          // arrived on cdone by then, so only the parity advances here
+          cx.par ^= 1u << (PB_CDONE + (b & 1));
+          break;
+        }
         if (ok) ok = warp_wait_busy(&bars.cdone[b & 1], pbit(cx.par, PB_CDONE + (b & 1)), lane, piece);
         cx.par ^= 1u << (PB_CDONE + (b & 1));
         if (ok) {
@@ -744,14 +753,17 @@ __device__ __forceinline__ bool mma_tile(const UnitState& us, uint8_t* smem, Mma
     return false;
   }
   if (nG > 0) {
-    // ---- FP32 refinement of the candidate delay cells (all warps) ----
+    // ---- last block's merge and FP32 refinement of the candidate delay
+    // cells (all warps, one segment at a time) ----
     // descending sigma: the largest windows (longest refinements) go first
+    const uint32_t* cml = colmax + (size_t)((NMB - 1) & 1) * kGemmSegs * kMRows;
     for (int sg = nsig - 1 - warp; sg >= 0; sg -= NW) {
       int l = gwin(0);
       for (int i = 1; i < nG; ++i)
         if (sg >= sig_base(gwin(i))) l = gwin(i);
       const int s = sg - sig_base(l);
       if (!seg_valid(l, s)) continue;
+      merge_block<PREC>(cml + sg * kMRows, NMB - 1, lst, lcount, runmax, sg, lane);
       const int nc = finish_list<PREC>(lst, lcount, runmax, sg, lane);
       int ci = lane >> 2;
       if (ci >= nc) ci = 0;
