@@ -213,6 +213,19 @@ __device__ __forceinline__ void store_keys(const UnitState& us, const unsigned l
 }
 
 
+// 8-byte asynchronous copy global -> shared (L1-cached); src_bytes 0
+// fills the destination with zeros and reads nothing.
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(__cvta_generic_to_global(src)), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // One pass of a work unit (baseline b, DM trial d, 32-AP tile) per delay
 // residue r.
 // Zero padding by pad_delay, with the band folded FOLD times, splits the
@@ -229,9 +242,11 @@ __device__ __forceinline__ void store_keys(const UnitState& us, const unsigned l
 // delay_stage runs stages 0-2 and leaves Y[t][m1 + N1 m2] (row pitch N + 1)
 // in S; the rate stage (FP32 register FFTs or the tensor-core GEMM) follows.
 // Called by every thread of the CTA after `us` has been filled and
-// synchronised; returns after a barrier, with Y complete in S.
-template <int N1, int FOLD, bool PK = true, bool PK2 = PK>
-__device__ __forceinline__ void delay_stage(const UnitState& us, float2* S) {
+// synchronised; returns after a barrier, with Y complete in S.  With AMAX,
+// the largest |Re| or |Im| of Y is also folded into *amax (an FP32 bit
+// pattern; non-negative floats order like their bits).
+template <int N1, int FOLD, bool PK = true, bool PK2 = PK, bool AMAX = false>
+__device__ __forceinline__ void delay_stage(const UnitState& us, float2* S, unsigned int* amax = nullptr) {
   constexpr int N = 32 * N1;
   // N1 a power of two (radix-2 register FFTs, each warp owns 32 / N1
   // consecutive k0) or 3 times one (mixed-radix FFTs, k0 = warp + N1 j)
@@ -255,29 +270,78 @@ __device__ __forceinline__ void delay_stage(const UnitState& us, float2* S) {
       constexpr int F = decltype(ff)::value;
       wf[F] = F == 0 ? make_float2(1.f, 0.f) : __ldg(tw_m + (N * F * r) % Mm);
     });
+    // Folded bands (FOLD > 1) read FOLD N-point sections per residue, more
+    // than the L1 keeps between residues: the first section of every k0
+    // this warp owns goes to S by asynchronous copies, all in flight at
+    // once and into the very slots S[t][k0 N1 + m1] that this thread later
+    // overwrites with its stage-1 outputs, so no other thread touches them
+    // (one copy group per k0); for FOLD = 2 section 1 is loaded while they
+    // land (with more sections that measured slower).
+    // Unfolded bands load directly: the copies measured slower there.
+    if constexpr (FOLD > 1) static_for<0, KPW>([&](auto jj) {
+      constexpr int J = decltype(jj)::value;
+      const int k0 = kPow2 ? warp * KPW + J : warp + N1 * J;
+      if (kPow2 || k0 < 32) {
+        static_for<0, N1>([&](auto kk1) {
+          constexpr int K1 = decltype(kk1)::value;
+          const int kf = k0 + 32 * K1;
+          const float2* src = tin ? xb + (size_t)kf * n_ap + t + __ldg(sh + kf) : xb;
+          cp_async8(S + lane * LD + k0 * N1 + K1, src, tin ? 8 : 0);
+        });
+      }
+      cp_async_commit();
+    });
     static_for<0, KPW>([&](auto jj) {
       constexpr int J = decltype(jj)::value;
       const int k0 = kPow2 ? warp * KPW + J : warp + N1 * J;
       if (!kPow2 && k0 >= 32) return;
+      // fold passes F >= 1 add the band's F-th N-point section (N1
+      // independent loads per pass), summed in the order F = 1, 2, ..
       float2 x[N1];
-      static_for<0, N1>([&](auto kk1) {
-        constexpr int K1 = decltype(kk1)::value;
-        const int k = k0 + 32 * K1;
-        float2 v = make_float2(0.f, 0.f);
-        static_for<0, FOLD>([&](auto ff) {
-          constexpr int F = decltype(ff)::value;
-          const int kf = k + N * F;
+      if constexpr (FOLD == 2) {
+        // section 1 is loaded before waiting for the copies of section 0
+        float2 u1[N1];
+        static_for<0, N1>([&](auto kk1) {
+          constexpr int K1 = decltype(kk1)::value;
+          const int kf = k0 + 32 * K1 + N;
+          u1[K1] = make_float2(0.f, 0.f);
+          if (tin) u1[K1] = __ldg(xb + (size_t)kf * n_ap + t + __ldg(sh + kf));
+        });
+        cp_async_wait<KPW - 1 - J>();
+        static_for<0, N1>([&](auto kk1) {
+          constexpr int K1 = decltype(kk1)::value;
+          x[K1] = cadd_t<PK>(S[lane * LD + k0 * N1 + K1], cmul(u1[K1], wf[1]));
+        });
+      } else if constexpr (FOLD > 2) {
+        cp_async_wait<KPW - 1 - J>();
+        static_for<0, N1>([&](auto kk1) {
+          constexpr int K1 = decltype(kk1)::value;
+          x[K1] = S[lane * LD + k0 * N1 + K1];
+        });
+      } else {
+        static_for<0, N1>([&](auto kk1) {
+          constexpr int K1 = decltype(kk1)::value;
+          const int kf = k0 + 32 * K1;
+          x[K1] = make_float2(0.f, 0.f);
+          if (tin) x[K1] = __ldg(xb + (size_t)kf * n_ap + t + __ldg(sh + kf));
+        });
+      }
+      static_for<FOLD == 2 ? 2 : 1, FOLD>([&](auto ff) {
+        constexpr int F = decltype(ff)::value;
+        static_for<0, N1>([&](auto kk1) {
+          constexpr int K1 = decltype(kk1)::value;
+          const int kf = k0 + 32 * K1 + N * F;
           float2 u = make_float2(0.f, 0.f);
           if (tin) u = __ldg(xb + (size_t)kf * n_ap + t + __ldg(sh + kf));
-          if constexpr (F == 0) {
-            v = u;
-          } else {
-            v = cadd_t<PK>(v, cmul(u, wf[F]));
-          }
+          x[K1] = cadd_t<PK>(x[K1], cmul(u, wf[F]));
         });
-        if (r != 0) v = cmul(v, __ldg(tw_m + k * r));  // k < N, r < P: k r < M
-        x[K1] = v;
       });
+      if (r != 0) {
+        static_for<0, N1>([&](auto kk1) {
+          constexpr int K1 = decltype(kk1)::value;
+          x[K1] = cmul(x[K1], __ldg(tw_m + (k0 + 32 * K1) * r));  // k < N, r < P: k r < M
+        });
+      }
       if constexpr (kPow2) {
         fft_dif<N1, PK>(x);
       } else {
@@ -301,6 +365,13 @@ __device__ __forceinline__ void delay_stage(const UnitState& us, float2* S) {
       y[K0] = S[lane * LD + K0 * N1 + warp];
     });
     fft_dif<32, PK2>(y);
+    if constexpr (AMAX) {
+      float m = 0.f;
+#pragma unroll
+      for (int i = 0; i < 32; ++i) m = fmaxf(m, fmaxf(fabsf(y[i].x), fabsf(y[i].y)));
+      const uint32_t wm = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
+      if (lane == 0) atomicMax(amax, wm);
+    }
     __syncthreads();
     static_for<0, 32>([&](auto mm2) {
       constexpr int M2 = decltype(mm2)::value;

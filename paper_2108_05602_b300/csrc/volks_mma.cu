@@ -497,7 +497,8 @@ __device__ __forceinline__ bool mma_tile(const UnitState& us, uint8_t* smem, Mma
   unsigned long long* best = reinterpret_cast<unsigned long long*>(smem + L::OFF_BEST);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-  delay_stage<N1, FOLD, false>(us, S);
+  // FP16 / FP8: the delay stage also folds max |Re|, |Im| of Y into s_amax
+  delay_stage<N1, FOLD, false, false, PREC != VOLKS_BF16>(us, S, reinterpret_cast<unsigned int*>(s_amax));
 
   const int win_mask = us.a.win_mask;
   const int t0 = us.t0, nv = us.nv, r = us.r;
@@ -536,14 +537,6 @@ __device__ __forceinline__ bool mma_tile(const UnitState& us, uint8_t* smem, Mma
   if (nG > 0) {
     if constexpr (PREC != VOLKS_BF16) {
       // per-tile power-of-two operand scale: largest |component| -> < 2^SCALE_EXP
-      float mx = 0.f;
-      for (int i = tid; i < 32 * N; i += NT) {
-        const float2 v = S[(i / N) * LD + (i % N)];
-        mx = tc::fmax3(mx, fabsf(v.x), fabsf(v.y));
-      }
-      const uint32_t wm = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
-      if (lane == 0) atomicMax(reinterpret_cast<unsigned int*>(s_amax), wm);
-      __syncthreads();
       const float amax = *s_amax;
       if (amax > 0.f && amax < 3.0e38f) {
         int e;
@@ -744,7 +737,8 @@ __device__ __forceinline__ bool mma_tile(const UnitState& us, uint8_t* smem, Mma
         }
       }
     }
-    if (ok)
+    // pieces still left go to every warp after the refinement
+    if (ok && nG == 0)
       while (piece()) {
       }
   }
@@ -781,6 +775,10 @@ __device__ __forceinline__ bool mma_tile(const UnitState& us, uint8_t* smem, Mma
       }
       const unsigned long long key = warp_key(pw, qq * M + (uint32_t)(c * P + r));
       if (lane == 0) best[slot_base(l) + s] = key;
+    }
+    // the exact 1- and 2-AP pieces the helper warps left: the warps with
+    // short refinements take them
+    while (piece()) {
     }
   }
   __syncthreads();
