@@ -20,8 +20,9 @@
 //           coarse |Z|^2 over the segment's rate cells; helper warps merge
 //           each block's cells within delta of the segment's running
 //           maximum into a candidate list (at most 8 are kept).
-//   w=1,2   exact FP32 windows on the CUDA cores, taken in pieces by the
-//           helper warps while they wait.
+//   w=1,2   exact FP32 windows on the CUDA cores, taken in pieces (one
+//           segment each) by the helper warps while they wait, the rest by
+//           every warp after its refinement.
 //   refine  the retained delay cells of every segment are re-evaluated in
 //           FP32 from S (all R rate cells of each: pre-twiddled w-point
 //           register FFTs, as the FP32 kernel computes them); the segment's
@@ -558,10 +559,12 @@ __device__ __forceinline__ bool mma_tile(const UnitState& us, uint8_t* smem, Mma
   // ---- the exact 1- and 2-AP windows as a pool of work pieces ----
   // The helper warps take pieces while the barrier they wait on is not yet
   // complete, and after their own work: piece p < n1p is a 1-AP segment, the
-  // next n2p are halves of 2-AP segments; each ends in one 64-bit atomicMax
-  // into the segment's key, so the order of the pieces does not matter.
+  // next n2p are 2-AP segments (halves and quarters of segments measured
+  // slower: each piece pays a counter atomic and a warp reduction); each
+  // ends in one 64-bit atomicMax into the segment's key, so the order of
+  // the pieces does not matter.
   const int n1p = (win_mask & 1) ? kTile : 0;
-  const int n2p = (win_mask & 2) ? kTile : 0;
+  const int n2p = (win_mask & 2) ? kTile / 2 : 0;
   auto piece = [&]() -> bool {
     int pc = 0;
     if (lane == 0) pc = atomicAdd(piece_next, 1);
@@ -584,19 +587,19 @@ __device__ __forceinline__ bool mma_tile(const UnitState& us, uint8_t* smem, Mma
       const unsigned long long key = warp_key(bp, (uint32_t)(bc * P + r));
       if (lane == 0) atomicMax(best + slot_base(0) + s, key);
     } else {
-      // 2-AP segment s, columns of half h: each column's largest rate cell
+      // 2-AP segment s: each column's largest rate cell
       // is r0 + max(|2 rx|, |2 ry|, |sqrt2 (rx + ry)|, |sqrt2 (ry - rx)|),
       // which equals the largest of the eight cells rate_cells_w2 gives
       // (rounding is monotonic); the lane's best column (the first on equal
       // powers) is then resolved to its cell once.
-      const int q = pc - n1p, s = q >> 1, h = q & 1;
+      const int s = pc - n1p;
       if (!seg_valid(1, s)) return true;
       const float2* y0p = S + (2 * s) * LD;
       const float2* y1p = y0p + LD;
       float bp = -1.f;
-      int bc = lane + 32 * h * (N1 / 2);
+      int bc = lane;
 #pragma unroll 4
-      for (int jj = h * (N1 / 2); jj < (h + 1) * (N1 / 2); ++jj) {
+      for (int jj = 0; jj < N1; ++jj) {
         const int c = lane + 32 * jj;
         const float2 y0 = y0p[c], y1 = y1p[c];
         const float r0 = fmaf(y1.y, y1.y, fmaf(y1.x, y1.x, cabs2(y0)));
