@@ -19,7 +19,8 @@
 //   coarse  the drain warps store per (segment, delay cell) the largest
 //           coarse |Z|^2 over the segment's rate cells; helper warps merge
 //           each block's cells within delta of the segment's running
-//           maximum into a candidate list (at most 8 are kept).
+//           maximum into a candidate list (the last block is merged by the
+//           warp that refines the segment; at most 8 are kept).
 //   w=1,2   exact FP32 windows on the CUDA cores, taken in pieces (one
 //           segment each) by the helper warps while they wait, the rest by
 //           every warp after its refinement.
