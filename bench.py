@@ -49,6 +49,16 @@ def _evn_1bl_32dm(synth):
     return dataclasses.replace(synth.evn(), n_bl=1, n_dm=32)
 
 
+def _band_1bl(n_chan):
+    # one baseline of 20,000 APs with the EVN scan's 8 IFs widened to
+    # n_chan channels each (1024 or 2048 points: folded delay transforms),
+    # 16 DM trials over 0..937.5
+    def make(synth):
+        import dataclasses
+        return dataclasses.replace(synth.evn(), n_bl=1, n_ap=20000, n_chan=n_chan, n_dm=16, dm_step=1000.0 / 16)
+    return make
+
+
 WORKLOADS = {
     # the EVN-scale scan the metric is quoted on
     "evn_fp32": lambda synth: synth.evn(),
@@ -62,6 +72,9 @@ WORKLOADS = {
     "evn_1bl_32dm_bf16": _evn_1bl_32dm,
     "evn_1bl_32dm_fp16": _evn_1bl_32dm,
     "evn_1bl_32dm_fp8": _evn_1bl_32dm,
+    # profiling cases of the large band classes (FOLD 2 and 4)
+    "band1024_1bl": _band_1bl(128),
+    "band2048_1bl": _band_1bl(256),
 }
 # volks_params.precision of each workload (VOLKS_FP32 = 0, BF16 = 1, FP16 = 2, FP8 = 3)
 PRECISION = {"evn_bf16": 1, "evn_fp16": 2, "evn_fp8": 3, "evn_1bl_32dm_bf16": 1, "evn_1bl_32dm_fp16": 2,
@@ -88,8 +101,8 @@ def workload_config(name, wl, trials):
             "n_dm": wl.n_dm, "dm": [wl.dm_lo, wl.dm_lo + wl.dm_step * (wl.n_dm - 1)],
             "windows": list(wl.windows), "pad_delay": wl.pad_delay, "pad_rate": wl.pad_rate,
             "trials_per_step": trials, "input_bytes": wl.n_bl * wl.n_ap * wl.n_f * 8,
-            "l2": "inputs larger than L2 (3.6 GB per step)" if wl.n_bl * wl.n_ap * wl.n_f * 8 > (126 << 20)
-            else "inputs smaller than L2"}
+            "l2": f"inputs larger than L2 ({wl.n_bl * wl.n_ap * wl.n_f * 8 / 1e9:.2f} GB per step)"
+            if wl.n_bl * wl.n_ap * wl.n_f * 8 > (126 << 20) else "inputs smaller than L2"}
 
 
 def trial_count(wl, nvalid) -> int:
@@ -232,6 +245,8 @@ def traffic_per_launch(wl, trials):
         return None
     if t.get("kernel_hash") != kernel_source_hash():
         return None
+    if wl.n_ap * wl.n_f * 8 != t["input_bytes"] // t["n_bl"]:
+        return None  # another baseline shape (band class): the capture does not apply
     reads = t["dram_read_bytes"] * wl.n_bl / t["n_bl"]
     writes = t["dram_write_bytes"] * trials / t["trials"]
     return {"bytes": reads + writes, "read": reads, "write": writes,
@@ -701,7 +716,8 @@ def run_volks(args):
         basis = (f"FP32 FMA: {n_sm} SMs (device) x {FP32_LANES} lanes x 2 x {mhz:.0f} MHz "
                  "(max SM clock, MEASURED_PEAKS.json)")
         if prec == 0:
-            roofline = {"bound": "alu", "kernel": "search_kernel<16,4>",
+            roofline = {"bound": "alu", "kernel": f"search_kernel<16,4,{max(1, wl.n_f // 512)}>"
+                        if wl.n_f >= 512 else "search_kernel",
                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                         "frac": achieved / peak, "traffic": traffic["bytes"] if traffic else None,
                         "traffic_basis": traffic["basis"] if traffic else None,
