@@ -2,6 +2,7 @@
 consume: deterministic for a seed, the shapes and layouts the boundary
 documents, and the statistics their models state (CPU)."""
 import numpy as np
+import pytest
 
 from paper_2108_05602_b300 import synth
 
@@ -67,3 +68,22 @@ def test_bench_flop_and_trial_counts_by_hand():
     wl = synth.small(n_bl=1, n_ap=10, n_if=4, n_chan=16, n_dm=1, windows=(1, 2))
     assert bench.algorithmic_flops(wl, [10]) == 294400.0
     assert bench.trial_count(wl, [10]) == 15
+
+
+def test_bench_traffic_scaling_applies_only_to_the_captured_baseline_shape():
+    """roofline.traffic scales the committed one-baseline DRAM capture:
+    reads by baselines, writes by trials, and only for workloads whose
+    baselines have the captured shape (58,594 APs x 512 points)."""
+    import json
+    import os
+    import bench
+    with open(os.path.join(bench.ROOT, "profiles", bench.TRAFFIC_FILE)) as f:
+        cap = json.load(f)
+    if cap.get("kernel_hash") != bench.kernel_source_hash():
+        pytest.skip("the committed capture predates the current kernel sources")
+    evn = bench.workload("evn_fp32")
+    t = bench.traffic_per_launch(evn, 2 * cap["trials"])
+    assert t["read"] == cap["dram_read_bytes"] * 15
+    assert t["write"] == cap["dram_write_bytes"] * 2
+    assert bench.traffic_per_launch(bench.workload("band1024_1bl"), cap["trials"]) is None
+    assert bench.traffic_per_launch(bench.workload("band2048_1bl"), cap["trials"]) is None
