@@ -283,6 +283,37 @@ def test_fp32_fallback_for_1d_and_small_bands():
                     assert np.array_equal(x, y)
 
 
+@pytest.mark.parametrize("pname", ["fp32"] + list(PRECS))
+def test_power_of_two_input_scale_commutes(pname):
+    """Without channel normalisation, multiplying the input by 2^k scales
+    every FP32 intermediate by 2^k exactly, so the FP32 search returns the
+    same cells with powers scaled by 2^2k.  The FP16 / FP8 forms scale each
+    tile's operands by a power of two chosen from its largest component, so
+    their rounded operands, coarse passes and candidates are the same too;
+    at 2^20 unscaled E4M3 operands (largest finite 448) would saturate."""
+    prec = {"fp32": V.VOLKS_FP32, **PRECS}[pname]
+    wl = synth.small(n_bl=1, n_ap=160, n_if=8, n_chan=64, n_dm=2, dm_step=30.0,
+                     windows=(1, 2, 4, 8, 16, 32))
+    vis, cal, _ = make_data(wl, seed=11)
+    ref = gpu_search(wl, vis, cal, normalize_chan=0, precision=prec)
+    for k in (20, -20):
+        g = gpu_search(wl, (vis * np.float32(2.0 ** k)).astype(np.complex64), cal, normalize_chan=0,
+                       precision=prec)
+        for d in range(wl.n_dm):
+            for wi in range(len(wl.windows)):
+                P0, q0, m0 = ref.peaks(0, d, wi)
+                P1, q1, m1 = g.peaks(0, d, wi)
+                assert np.array_equal(q1, q0) and np.array_equal(m1, m0), (k, d, wi)
+                assert np.array_equal(P1, (P0 * np.float32(2.0 ** (2 * k))).astype(np.float32)), (k, d, wi)
+        c0, c1 = ref.candidates(), g.candidates()
+        assert [(c["bl"], c["dm_idx"], c["win"], c["seg"]) for c in c1] == \
+               [(c["bl"], c["dm_idx"], c["win"], c["seg"]) for c in c0]
+        for a, b in zip(c0, c1):
+            assert math.isclose(b["z"], a["z"], rel_tol=1e-12, abs_tol=1e-12)
+        g.close()
+    ref.close()
+
+
 def test_deterministic_bitwise():
     wl = synth.small(n_bl=1, n_ap=200, n_if=8, n_chan=64, n_dm=3, dm_step=20.0,
                      windows=(1, 2, 4, 8, 16, 32))
