@@ -196,6 +196,9 @@ CONFIGS = [
          windows=(2, 4, 8, 16, 32)),
     dict(name="nf2048_w2-32", n_bl=1, n_ap=100, n_if=16, n_chan=128, n_dm=2, dm_step=40.0,
          windows=(2, 8, 32)),
+    # DM trials 400 and 800 shift the band by more than its 40 APs: no valid AP
+    dict(name="nf256_nvalid0", n_bl=1, n_ap=40, n_if=8, n_chan=32, n_dm=3, dm_step=400.0,
+         windows=(1, 4, 32)),
 ]
 
 
@@ -267,13 +270,15 @@ def test_all_zero_input_ties_to_cell_zero():
 
 
 def test_fp32_fallback_for_1d_and_small_bands():
-    """1-D searches and bands under 256 points run the FP32 kernel whatever
-    precision is asked: results equal the FP32 search bit for bit."""
-    for kw in (dict(n_if=4, n_chan=32, pad_rate=4), dict(n_if=8, n_chan=32, pad_rate=0)):
+    """1-D searches, bands under 256 points and sliding segments (stride 1)
+    run the FP32 kernel whatever precision is asked: results equal the FP32
+    search bit for bit."""
+    for kw in (dict(n_if=4, n_chan=32, pad_rate=4, stride=0), dict(n_if=8, n_chan=32, pad_rate=0, stride=0),
+               dict(n_if=8, n_chan=64, pad_rate=4, stride=1)):
         import dataclasses
         wl = synth.small(n_bl=1, n_ap=150, n_if=kw["n_if"], n_chan=kw["n_chan"], n_dm=2,
                          windows=(1, 4, 16))
-        wl = dataclasses.replace(wl, pad_rate=kw["pad_rate"])
+        wl = dataclasses.replace(wl, pad_rate=kw["pad_rate"], stride=kw["stride"])
         vis, cal, _ = make_data(wl, seed=4)
         a = gpu_search(wl, vis, cal)
         b = gpu_search(wl, vis, cal, precision=V.VOLKS_BF16)
