@@ -61,6 +61,19 @@ constexpr int kPerBlk = 6;           // most delay cells a 128-cell block adds t
 constexpr int kList = 24;            // candidate list length per segment (>= 4 blocks x kPerBlk)
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
+// Helper warps during the GEMM phase.  With two drain warpgroups the
+// issuing warp's scheduler (warps 0, 4, 8, 12: warp % 4 picks it, and the
+// drain warps' TMEM lane quarters fix theirs) also runs two drain warps;
+// for BF16 / FP16 (four MMAs per job) warp 12 sits the phase out so the
+// issuing thread waits less for issue slots (BF16 measured 1.7 % faster,
+// FP16 the same); for FP8 (two MMAs per job) the seventh helper is worth
+// more (0.9 %).
+template <int NW, int NWG, int PREC>
+struct Helpers {
+  static constexpr bool kSpare = NWG == 2 && PREC != VOLKS_FP8;
+  static constexpr int count = NW - 1 - 4 * NWG - (kSpare ? 1 : 0);
+};
+
 template <int PREC>
 struct Op {
   static constexpr int EB = PREC == VOLKS_FP8 ? 1 : 2;      // bytes per element
@@ -474,7 +487,8 @@ __device__ __forceinline__ int finish_list(uint2* lst, const int* lcount, const 
 //                    whole job for its 32 TMEM lanes (lane quarter = warp % 4)
 //                    and stores per-(segment, delay cell) coarse maxima into
 //                    one of two column-maxima buffers (by block parity);
-//   helper warps     the others: the exact 1- and 2-AP windows, the A blocks
+//   helper warps     the others (but warp 12 for BF16 / FP16, see Helpers):
+//                    the exact 1- and 2-AP windows, the A blocks
 //                    from the third on (once `adone` says the MMAs reading the
 //                    buffer are complete), and the candidate merges of each
 //                    block but the last (once every drain warp passed
@@ -488,7 +502,7 @@ __device__ __forceinline__ bool mma_tile(const UnitState& us, uint8_t* smem, Mma
   using L = MmaSmem<N1, PREC>;
   constexpr int N = 32 * N1, LD = N + 1, NT = N, NW = N1, NMB = N / kMRows;
   constexpr int NWG = NW >= 16 ? 2 : 1;      // drain warpgroups
-  constexpr int NHELP = NW - 1 - 4 * NWG;    // helper warps
+  constexpr int NHELP = Helpers<NW, NWG, PREC>::count;
   static_assert(NHELP >= 1 && NMB >= 2, "work split");
   float2* S = reinterpret_cast<float2*>(smem);
   uint8_t* A = smem + L::OFF_A;
@@ -705,8 +719,9 @@ __device__ __forceinline__ bool mma_tile(const UnitState& us, uint8_t* smem, Mma
     }
   } else {
     // ---- helper warps ----
-    const int hw = warp < 4 ? warp - 1 : warp - 4 - 4 * NWG + 3;
-    if (nG > 0) {
+    constexpr bool kSpare = Helpers<NW, NWG, PREC>::kSpare;
+    const int hw = warp < 4 ? warp - 1 : warp - 4 - 4 * NWG + 3 - (kSpare ? 1 : 0);
+    if (nG > 0 && !(kSpare && warp == 12)) {
 #pragma unroll 1
       for (int b = 0; b < NMB; ++b) {
         if (b + 2 < NMB) {
@@ -810,7 +825,7 @@ __global__ void __launch_bounds__(32 * N1, 1) search_mma_kernel(const __grid_con
   using L = MmaSmem<N1, PREC>;
   build_rate_dft<PREC, 2>(smem + L::OFF_B, p.d[0].tw_m, p.d[0].M, tid, N);
   if (tid == 0) {
-    constexpr int NWG = N1 >= 16 ? 2 : 1, NHELP = N1 - 1 - 4 * NWG;
+    constexpr int NWG = N1 >= 16 ? 2 : 1, NHELP = Helpers<N1, NWG, PREC>::count;
     for (int l = 2; l <= 5; ++l) {
       jt.bd[l] = tc::sdesc_sw(tc::smem_u32(smem + L::OFF_B + Op<PREC>::b_off(l) - Op<PREC>::b_off(2)),
                               (uint32_t)Op<PREC>::b_row_bytes(l));
