@@ -213,6 +213,14 @@ __device__ __forceinline__ void store_keys(const UnitState& us, const unsigned l
 }
 
 
+// max of three floats in one instruction (NaN operands are ignored, as by
+// fmaxf)
+__device__ __forceinline__ float fmax3_f(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+
 // 8-byte asynchronous copy global -> shared (L1-cached); src_bytes 0
 // fills the destination with zeros and reads nothing.
 __device__ __forceinline__ void cp_async8(void* dst, const void* src, int src_bytes) {
@@ -365,18 +373,21 @@ __device__ __forceinline__ void delay_stage(const UnitState& us, float2* S, unsi
       y[K0] = S[lane * LD + K0 * N1 + warp];
     });
     fft_dif<32, PK2>(y);
-    if constexpr (AMAX) {
-      float m = 0.f;
-#pragma unroll
-      for (int i = 0; i < 32; ++i) m = fmaxf(m, fmaxf(fabsf(y[i].x), fabsf(y[i].y)));
-      const uint32_t wm = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
-      if (lane == 0) atomicMax(amax, wm);
-    }
     __syncthreads();
     static_for<0, 32>([&](auto mm2) {
       constexpr int M2 = decltype(mm2)::value;
       S[lane * LD + warp + N1 * M2] = y[bitrev(M2, 5)];
     });
+    if constexpr (AMAX) {
+      // four independent chains of 3-input maxima (one serial chain of 64
+      // maxima measured ~4 % of the tensor-core kernel's time)
+      float m[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int i = 0; i < 32; ++i) m[i & 3] = fmax3_f(m[i & 3], fabsf(y[i].x), fabsf(y[i].y));
+      const float mm = fmaxf(fmaxf(m[0], m[1]), fmaxf(m[2], m[3]));
+      const uint32_t wm = __reduce_max_sync(0xffffffffu, __float_as_uint(mm));
+      if (lane == 0) atomicMax(amax, wm);
+    }
   }
   __syncthreads();
 }
